@@ -1,0 +1,355 @@
+"""Benchmark of the random-circuit-sampling hot path on GB300.
+
+One step = the whole path on one circuit: reset the state to |0...0>, apply the
+fused circuit (tensor-core BF16x3 passes), draw the shots, score them with
+linear XEB. Default workload: 34 qubits on a 5x7 grid minus one corner,
+20 cycles, coupler pattern ABCDCDAB, 10^6 shots (128 GiB complex64 state).
+
+Prints one JSON line (rank 0). `value` is seconds per circuit (lower is better),
+device-resident inputs; `e2e` times the same step through the public host-buffer
+calls (gate list uploaded, samples copied back and re-uploaded for XEB).
+`--impl reference` times the CPU oracle instead (bounded sample, see below).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2512_07311_gb300 import circuits as C  # noqa: E402
+
+METRIC = "34q 20-cycle circuit time (s), shots/s; fused-TC vs plain FP32 at 1e-5 infid"
+WORKLOAD = "34q_5x7m1_20cyc"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(C.CONFIGS))
+    ap.add_argument("--shots", type=int, default=None)
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP32 plain/fused comparison runs")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: str):
+        self.proc = None
+        self.gpu = gpu  # nvidia-smi -i accepts an index or a UUID
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ peaks
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+# ------------------------------------------------------------------ CPU oracle baseline
+
+def cpu_baseline(circ: C.Circuit, shots: int, budget_s: float = 20.0) -> dict:
+    """Times the CPU oracle (as it stands) on a bounded sample of the workload:
+    the workload's own gate sequence applied, in order, to a 2^n_s-amplitude
+    complex128 state (qubit q acts as q mod n_s; gates that collapse onto one
+    qubit are skipped), then the oracle's inverse-CDF sampler and XEB. Times are
+    scaled to the full workload by 2^(n - n_s) and by gates applied."""
+    from oracle import oracle as O
+
+    O.build()
+    n = circ.n_qubits
+    n_s = min(n, 26)
+    g = circ.gates.copy()
+    g["q0"] %= n_s
+    two = g["nq"] == 2
+    g["q1"][two] %= n_s
+    keep = ~(two & (g["q0"] == g["q1"]))
+    g = g[keep]
+    psi = O.zero_state(n_s)
+    t0 = time.perf_counter()
+    done = 0
+    step = 8
+    while done < len(g) and time.perf_counter() - t0 < budget_s * 0.7:
+        O.run(psi, g[done:done + step])
+        done += min(step, len(g) - done)
+    t_apply = time.perf_counter() - t0
+    s_shots = min(shots, 100_000)
+    t1 = time.perf_counter()
+    xs = O.sample(psi, s_shots, seed=1)
+    t_sample = time.perf_counter() - t1
+    t2 = time.perf_counter()
+    O.xeb(psi, xs)
+    t_xeb = time.perf_counter() - t2
+    scale = 2.0 ** (n - n_s)
+    # sampling = one 2^n CDF pass (dominant) + shots * log2(2^n) searches; scale the pass by 2^(n-n_s)
+    est = t_apply * scale * len(circ.gates) / max(done, 1) + t_sample * scale + t_xeb * shots / s_shots
+    return {"value": est, "unit": "s", "cores": O.threads(), "kind": "oracle",
+            "sample": (f"oracle on a 2^{n_s}-amplitude complex128 state: first {done} of {len(circ.gates)} "
+                       f"workload gates (qubit q -> q mod {n_s}), {s_shots} shots + XEB; "
+                       f"scaled x2^{n - n_s} per amplitude pass and by gate count"),
+            "measured_s": {"apply": t_apply, "sample": t_sample, "xeb": t_xeb}}
+
+
+# ------------------------------------------------------------------ reference arm (the CPU oracle)
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    cfg = C.CONFIGS[args.workload]
+    circ = C.config_circuit(args.workload)
+    shots = args.shots or cfg["shots"]
+    for _ in range(args.warmup):
+        cpu_baseline(circ, shots, budget_s=3.0)
+    vals = [cpu_baseline(circ, shots, budget_s=10.0) for _ in range(args.steps)]
+    v = statistics.median(x["value"] for x in vals)
+    line = {"metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "qubits": circ.n_qubits, "cycles": circ.cycles,
+                       "pattern": circ.pattern, "shots": shots},
+            "cpu_baseline": {k: vals[-1][k] for k in ("kind", "cores", "sample")} | {"value": v, "unit": "s"},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+
+    from paper_2512_07311_gb300 import build as B
+    from paper_2512_07311_gb300 import capi
+
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    B.build()
+    capi.load()
+    cfg = C.CONFIGS[args.workload]
+    circ = C.config_circuit(args.workload)
+    n = circ.n_qubits
+    shots = args.shots or cfg["shots"]
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ctx = capi.rcs_create(circ.grid, capi.RCS_PREC_BF16X3, stream=sh)
+    plan = capi.rcs_plan_build(n, circ.gates, capi.RCS_PREC_BF16X3)
+    info = capi.rcs_plan_info(plan)
+    capi.rcs_plan_upload(ctx, plan)
+    d_bits = torch.empty(shots, dtype=torch.int64, device="cuda")
+    d_xeb = torch.empty(1, dtype=torch.float64, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    apply_ms, sample_ms, xeb_ms = [], [], []
+
+    def step(seed, timed):
+        ev[0].record(stream)
+        capi.rcs_reset(ctx)
+        capi.rcs_plan_run(ctx, plan)
+        ev[1].record(stream)
+        capi.rcs_sample_device(ctx, shots, seed, d_bits.data_ptr())
+        ev[2].record(stream)
+        capi.rcs_xeb_device(ctx, d_bits.data_ptr(), shots, d_xeb.data_ptr())
+        ev[3].record(stream)
+        if timed:
+            stream.synchronize()
+            apply_ms.append(ev[0].elapsed_time(ev[1]))
+            sample_ms.append(ev[1].elapsed_time(ev[2]))
+            xeb_ms.append(ev[2].elapsed_time(ev[3]))
+
+    for w in range(args.warmup):
+        step(1000 + w, False)
+    capi.rcs_sync(ctx)
+    barrier()
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        gpu_id = str(local)
+    with ClockSampler(gpu_id) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        barrier()
+        t_start.record(stream)
+        for s in range(args.steps):
+            step(s, False)
+        t_end.record(stream)
+        barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    capi.rcs_sync(ctx)
+    # per-phase breakdown from a separate, identical set of steps
+    for s in range(min(args.steps, 3)):
+        step(s, True)
+    ms_step = total_ms / args.steps
+    t_local = torch.tensor([ms_step], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    ms_step = float(t_local.item())
+    F = float(d_xeb.item())
+
+    # roofline of the dominant kernel (the tensor-core pass): algorithmic bytes per launch / mean launch time
+    peaks = measured_peaks()
+    passes = int(info["n_passes"])
+    t_pass_s = statistics.median(apply_ms) / 1e3 / passes
+    bytes_per_launch = 16.0 * 2.0**n
+    achieved = bytes_per_launch / t_pass_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "kernel": "k_fused_tc", "peak_src": peaks["src"],
+                "algorithmic_bytes_per_launch": bytes_per_launch, "launches_per_step": passes}
+
+    # end to end through the host-buffer API: gate list in, samples out, samples in, XEB out
+    e2e_ms = []
+    for s in range(max(1, min(args.steps, 3))):
+        barrier()
+        t0 = time.perf_counter()
+        capi.rcs_reset(ctx)
+        capi.rcs_apply_circuit(ctx, circ.gates)
+        xs = capi.rcs_sample(ctx, shots, 77 + s)
+        F_e2e = capi.rcs_xeb(ctx, xs)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    h2d = circ.gates.nbytes + passes * 65536 + shots * 8
+    d2h = shots * 8 + 8
+
+    compare = {}
+    if not args.no_compare:
+        # same circuit through the plain FP32 per-gate path and the fused FP32 path (one run each),
+        # and the subset infidelity of the TC state against each on a seeded 2^20-amplitude subset
+        rng = np.random.default_rng(2**20)
+        subset = np.unique(rng.integers(0, 1 << n, size=1 << 20, dtype=np.uint64))
+        capi.rcs_reset(ctx)
+        capi.rcs_plan_run(ctx, plan)
+        a_tc = capi.rcs_amplitudes(ctx, subset)
+        for name, prec, kmax in (("fp32_plain", capi.RCS_PREC_FP32_PLAIN, 0), ("fp32_fused_k4", capi.RCS_PREC_FP32_FUSED, 4)):
+            p2 = capi.rcs_plan_build(n, circ.gates, prec, kmax)
+            i2 = capi.rcs_plan_info(p2)
+            capi.rcs_plan_upload(ctx, p2)
+            capi.rcs_reset(ctx)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            capi.rcs_plan_run(ctx, p2)
+            e1.record(stream)
+            capi.rcs_sync(ctx)
+            t = e0.elapsed_time(e1) / 1e3
+            a = capi.rcs_amplitudes(ctx, subset)
+            ov = abs(np.vdot(a, a_tc)) ** 2 / (np.vdot(a, a).real * np.vdot(a_tc, a_tc).real)
+            compare[name] = {"apply_s": t, "passes": int(i2["n_passes"]),
+                             "hbm_frac": 16.0 * 2**n * i2["n_passes"] / t / 1e9 / peaks["hbm_gbs"],
+                             "subset_infidelity_vs_bf16x3": 1.0 - ov}
+            capi.rcs_plan_destroy(p2)
+        compare["bf16x3_apply_s"] = statistics.median(apply_ms) / 1e3
+        compare["speedup_vs_fp32_plain"] = compare["fp32_plain"]["apply_s"] / compare["bf16x3_apply_s"]
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(circ, shots)
+
+    capi.rcs_plan_destroy(plan)
+    capi.rcs_destroy(ctx)
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": ms_step / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16x3 (fp32 accumulate); fp32 state; exact fixed-point/f64 reductions",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "qubits": n, "cycles": circ.cycles, "pattern": circ.pattern,
+                       "grid": f"{circ.grid.rows}x{circ.grid.cols}-{len(circ.grid.removed)}", "shots": shots,
+                       "gates": len(circ.gates), "passes": passes, "precision": "bf16x3",
+                       "state_bytes": 8 * 2**n, "l2": "inputs larger than L2 (state 128 GiB)",
+                       "parallelism": f"replicas{world}" if world > 1 else "single"},
+            "shots_per_s": shots / (statistics.median(sample_ms) / 1e3),
+            "phases_ms": {"reset+apply": statistics.median(apply_ms), "sample": statistics.median(sample_ms),
+                          "xeb": statistics.median(xeb_ms)},
+            "xeb": F, "xeb_e2e": F_e2e,
+            "roofline": roofline,
+            "e2e": {"value": statistics.median(e2e_ms) / 1e3, "unit": "s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": 1 + passes + 1 + 3 + 1 + 2,
+            "clocks": clocks,
+            "compare": compare,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

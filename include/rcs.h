@@ -1,0 +1,230 @@
+/*
+ * rcs.h -- C ABI of the GB300 random-circuit-sampling state-vector library.
+ *
+ * The library implements, on one GPU, the three stages of the hybrid pipeline
+ * of Wold & Kasirajan, "Revisiting Quantum Supremacy: Simulating Sycamore-Class
+ * Circuits Using Hybrid CPU/GPU HPC Workloads" (Section 3.2, items 1, 3, 4):
+ * quantum state construction from a circuit, measurement sampling of many
+ * shots, and the linear cross-entropy benchmark (XEB) of the samples. The paper
+ * runs the first stage on a GPU and the other two as CPU jobs; here all three
+ * are CUDA kernels on a dense complex64 state vector held in HBM.
+ *
+ * Conventions (the paper fixes none of them):
+ *  - qubit q is bit q of the basis index (qubit 0 = least significant bit);
+ *  - the state is 2^n complex64 amplitudes, interleaved (re, im), 8 bytes each;
+ *  - a gate on targets (t0, t1) uses local index j = bit(t0) + 2 bit(t1);
+ *  - bitstrings are uint64 basis indices (bit q = qubit q), n <= 34.
+ *
+ * Errors: every int-returning call returns RCS_OK (0) or a negative RCS_ERR_*
+ * code and never aborts the process; rcs_last_error() gives a message. A call
+ * that fails argument validation leaves the state unchanged.
+ *
+ * Ownership: every pointer argument is owned by the caller. Host arrays are
+ * read (or written) only during the call. Pointers documented as DEVICE must
+ * be device memory of the context's GPU. The device state is owned by the
+ * context and freed by rcs_destroy().
+ *
+ * Streams: all device work of a context is issued on its stream (rcs_opts.stream,
+ * a cudaStream_t; 0 = the legacy default stream). Calls taking or returning HOST
+ * data synchronise that stream before returning; calls on DEVICE pointers only
+ * enqueue work and return.
+ */
+#ifndef RCS_H
+#define RCS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes */
+#define RCS_OK 0
+#define RCS_ERR_ARG (-1)         /* malformed argument (null pointer, bad size, non-unitary matrix) */
+#define RCS_ERR_QUBIT (-2)       /* qubit index out of range, or repeated within a gate */
+#define RCS_ERR_OOM (-3)         /* device allocation failed */
+#define RCS_ERR_CUDA (-4)        /* a CUDA runtime call failed (message has the CUDA error) */
+#define RCS_ERR_TIMEOUT (-5)     /* a bounded device-side wait ran out; the kernel returned early */
+#define RCS_ERR_UNSUPPORTED (-6) /* valid request this build cannot serve (e.g. no sm_103 GPU) */
+
+/* ---- gate kinds (the Sycamore-class gate set; matrices below) */
+#define RCS_GATE_SQRT_X 0 /* ((1+i) I + (1-i) X) / 2 */
+#define RCS_GATE_SQRT_Y 1 /* ((1+i) I + (1-i) Y) / 2 */
+#define RCS_GATE_SQRT_W 2 /* ((1+i) I + (1-i) W) / 2, W = (X + Y) / sqrt(2) */
+#define RCS_GATE_FSIM 3   /* [[1,0,0,0],[0,c,-is,0],[0,-is,c,0],[0,0,0,e^{-i phi}]], c = cos theta, s = sin theta */
+#define RCS_GATE_U1 4     /* caller's 2x2 unitary in rcs_gate.u */
+#define RCS_GATE_U2 5     /* caller's 4x4 unitary in rcs_gate.u (local index j = bit(q[0]) + 2 bit(q[1])) */
+
+#define RCS_FLAG_ADJOINT 1 /* apply the conjugate transpose of the gate */
+
+/* ---- numerical paths for the state update */
+#define RCS_PREC_FP32_PLAIN 0 /* one kernel launch per gate, FP32 SIMT (the baseline path) */
+#define RCS_PREC_FP32_FUSED 1 /* gates fused into k-qubit unitaries (k <= k_max <= 5), FP32 SIMT */
+#define RCS_PREC_BF16X3 2     /* fused 6-qubit unitaries on tcgen05 tensor cores, BF16 hi/lo split, 3 products, FP32 accumulate */
+
+typedef struct rcs_ctx rcs_ctx;
+typedef struct rcs_plan rcs_plan;
+
+/* Grid of qubits: rows x cols cells, minus `n_removed` cells whose row-major ids
+ * are in `removed`. Only the qubit count n = rows*cols - n_removed matters to the
+ * simulator; the circuit's gates name qubits by index. */
+typedef struct {
+    int32_t rows, cols, n_removed;
+    const int32_t *removed;
+} rcs_grid;
+
+/* One gate. nq = 1 or 2 (must match kind). q[1] is ignored when nq = 1. theta and
+ * phi are used by RCS_GATE_FSIM only. u (U1/U2 only) points to 2^nq x 2^nq
+ * complex128 entries, row-major, interleaved (re, im); it must be unitary to
+ * 1e-6. 40 bytes, naturally aligned. */
+typedef struct {
+    uint8_t kind, nq, flags, reserved;
+    int32_t q[2];
+    double theta, phi;
+    const double *u;
+} rcs_gate;
+
+/* Options. precision: RCS_PREC_*. k_max: largest fused block (FP32_FUSED: 2..5,
+ * default 4; BF16X3: 6). autotune: 1 = choose k_max by timed trials on first use
+ * for this qubit count and precision. stream: cudaStream_t for all device work. */
+typedef struct {
+    int32_t precision;
+    int32_t k_max;
+    int32_t autotune;
+    int32_t reserved;
+    uint64_t stream;
+} rcs_opts;
+
+/* Description of a built plan (rcs_plan_info). */
+typedef struct {
+    int32_t n_qubits;
+    int32_t precision;
+    int64_t n_gates;
+    int64_t n_passes;
+    int32_t k_max;        /* largest block width used */
+    int32_t reserved;
+    double hbm_bytes;     /* algorithmic HBM bytes: 16 * 2^n per pass */
+    double flops;         /* algorithmic real flops of all passes (x3 for the split-precision path) */
+} rcs_plan_stats;
+
+/* ------------------------------------------------------------------ context */
+
+/* Creates a context for n = rows*cols - n_removed qubits (1 <= n <= 34) on the
+ * current CUDA device and sets the state to |0...0> (Section 3.2 item 1 starts
+ * from the all-zero state of the circuit's qubits). Allocates 8 * 2^n bytes of
+ * state plus the sampler's block sums (2^n / 1024 * 24 bytes). opts may be NULL
+ * (FP32_FUSED, k_max 4, legacy stream). Returns RCS_ERR_OOM if the state does
+ * not fit in device memory. */
+int rcs_create(const rcs_grid *grid, const rcs_opts *opts, rcs_ctx **out);
+
+/* Releases the context and its device memory. NULL is a no-op. */
+void rcs_destroy(rcs_ctx *ctx);
+
+/* Last error message for ctx, or for the calling thread when ctx is NULL. */
+const char *rcs_last_error(const rcs_ctx *ctx);
+
+/* Number of qubits of the context. */
+int rcs_num_qubits(const rcs_ctx *ctx);
+
+/* Changes the stream used for the context's device work (cudaStream_t). */
+int rcs_set_stream(rcs_ctx *ctx, uint64_t stream);
+
+/* Resets the state to |0...0> (asynchronous on the context's stream). */
+int rcs_reset(rcs_ctx *ctx);
+
+/* ------------------------------------------------------------------ state construction (Section 3.2 item 1) */
+
+/* Applies the n_gates host gates, in order, to the current state (psi <- U_G ... U_1 psi).
+ * The gate list is validated (kinds, qubit range, distinct targets, unitarity of
+ * U1/U2), fused by the planner of the context's precision into passes, uploaded
+ * and launched. The gate array may be freed when the call returns; the launches
+ * are asynchronous on the context's stream. */
+int rcs_apply_circuit(rcs_ctx *ctx, const rcs_gate *gates, size_t n_gates);
+
+/* Applies one dense k-qubit unitary (1 <= k <= 6) to targets[0..k-1] (distinct,
+ * local index j = sum_i bit(targets[i]) 2^i); u_re_im holds 2^k x 2^k complex128
+ * entries, row-major, interleaved, unitary to 1e-6. k <= 5 runs the FP32 fused
+ * kernel; k = 6 needs the BF16X3 precision and n >= 13 (tensor-core kernel),
+ * else RCS_ERR_UNSUPPORTED. Asynchronous. */
+int rcs_apply_unitary(rcs_ctx *ctx, int k, const int32_t *targets, const double *u_re_im);
+
+/* Host-only planning (no GPU needed): fuses the gates into passes for an n-qubit
+ * state with the given options (NULL = FP32_FUSED, k_max 4). The plan keeps its
+ * own copy of everything it needs. */
+int rcs_plan_build(int n_qubits, const rcs_gate *gates, size_t n_gates, const rcs_opts *opts, rcs_plan **out);
+
+/* Statistics of a plan. */
+int rcs_plan_info(const rcs_plan *plan, rcs_plan_stats *out);
+
+/* Pass i of a plan: *k targets written to targets[0..k-1] (ascending; local index
+ * j = sum_i bit(targets[i]) 2^i) and, if u_re_im is not NULL, its 2^k x 2^k matrix
+ * (row-major complex128, interleaved) as planned in FP64. targets must hold 8 ints,
+ * u_re_im 2 * 4^k doubles. */
+int rcs_plan_pass(const rcs_plan *plan, size_t i, int32_t *k, int32_t *targets, double *u_re_im);
+
+/* Uploads the plan's pass table and matrices to the device of ctx (once per plan
+ * and context; later calls are no-ops). */
+int rcs_plan_upload(rcs_ctx *ctx, rcs_plan *plan);
+
+/* Launches every pass of an uploaded plan on the current state (asynchronous). */
+int rcs_plan_run(rcs_ctx *ctx, rcs_plan *plan);
+
+/* Frees a plan and its device copies. NULL is a no-op. */
+void rcs_plan_destroy(rcs_plan *plan);
+
+/* ------------------------------------------------------------------ readout */
+
+/* Gathers amplitudes psi[bits[i]] into out_re_im[2i], out_re_im[2i+1] (complex64
+ * promoted exactly to complex128). Synchronous. bits[i] < 2^n or RCS_ERR_ARG. */
+int rcs_amplitudes(rcs_ctx *ctx, const uint64_t *bits, size_t n, double *out_re_im);
+
+/* Copies amplitudes [first, first+count) of the state to host floats (interleaved
+ * re, im; 2*count floats). Synchronous. */
+int rcs_state_read(rcs_ctx *ctx, uint64_t first, uint64_t count, float *out_re_im);
+
+/* Overwrites amplitudes [first, first+count) from host floats. Synchronous. */
+int rcs_state_write(rcs_ctx *ctx, uint64_t first, uint64_t count, const float *in_re_im);
+
+/* Device address of the state (2^n complex64, interleaved). The context keeps
+ * ownership; writes through it must be followed by no other call of this API
+ * until they are complete on the context's stream. */
+int rcs_state_device(rcs_ctx *ctx, void **d_state);
+
+/* Synchronises the context's stream and reports device-side errors raised by
+ * earlier asynchronous calls (RCS_ERR_TIMEOUT for a bounded wait that ran out,
+ * RCS_ERR_ARG for an out-of-range bitstring or an unusable state), then clears them. */
+int rcs_sync(rcs_ctx *ctx);
+
+/* T = sum_i |psi_i|^2, reduced exactly in 2^-62 fixed point and returned as double.
+ * Synchronous. */
+int rcs_norm(rcs_ctx *ctx, double *out);
+
+/* ------------------------------------------------------------------ sampling (Section 3.2 item 3) */
+
+/* Draws `shots` samples x_s = smallest i with C_i > u_s * T, where C_i = sum_{j<=i}
+ * |psi_j|^2, T = C_{2^n-1} (prefix sums exact in 2^-62 fixed point), and u_s is
+ * word (s mod 4) of Philox4x64-10(counter = (s div 4, 0, 0, 0), key = (seed, 0))
+ * mapped to [0,1) as (x >> 11) 2^-53. Zero-probability indices are never drawn.
+ * Writes shots uint64 indices to HOST out_bits. Synchronous. The state must
+ * have norm < 3.9 (unitary circuits keep it at 1). */
+int rcs_sample(rcs_ctx *ctx, uint64_t shots, uint64_t seed, uint64_t *out_bits);
+
+/* As rcs_sample, writing to DEVICE memory d_out_bits; asynchronous. */
+int rcs_sample_device(rcs_ctx *ctx, uint64_t shots, uint64_t seed, uint64_t *d_out_bits);
+
+/* ------------------------------------------------------------------ scoring (Section 3.2 item 4) */
+
+/* Linear XEB of the samples against the current state:
+ * F = 2^n * (1/N) sum_s |psi_{x_s}|^2 / T - 1, reduced in FP64. HOST samples,
+ * HOST result. Synchronous. A sample >= 2^n gives RCS_ERR_ARG. */
+int rcs_xeb(rcs_ctx *ctx, const uint64_t *samples, size_t n, double *out_xeb);
+
+/* As rcs_xeb with DEVICE samples and a DEVICE double result; asynchronous.
+ * An out-of-range sample makes the result NaN. */
+int rcs_xeb_device(rcs_ctx *ctx, const uint64_t *d_samples, size_t n, double *d_out_xeb);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RCS_H */

@@ -1,0 +1,623 @@
+// C ABI of the library (include/rcs.h): context and device memory, validation,
+// planning, pass launches, sampling and scoring calls.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "dev_common.cuh"
+#include "internal.h"
+
+using namespace rcs;
+
+struct rcs_ctx {
+    int n = 0;
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    rcs_opts opts{};
+    float2 *psi = nullptr;
+    uint64_t *bsum = nullptr, *bpre = nullptr, *chunk = nullptr, *total = nullptr;
+    int *d_err = nullptr;
+    bool sums_valid = false;  // bsum/bpre/total describe the current state
+    // growable scratch for host-provided arrays and results
+    uint64_t *d_u64 = nullptr;
+    size_t u64_cap = 0;
+    double *d_f64 = nullptr;
+    size_t f64_cap = 0;
+    uint8_t *d_ops = nullptr;  // tensor-core operand images of rcs_apply_circuit plans
+    size_t ops_cap = 0;
+    std::string err;
+};
+
+struct rcs_plan {
+    Plan p;
+    uint8_t *d_ops = nullptr;
+    int d_ops_dev = -1;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(rcs_ctx *ctx, int code, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    else g_err = msg;
+    return code;
+}
+
+int cuda_fail(rcs_ctx *ctx, cudaError_t e, const char *what) {
+    return fail(ctx, e == cudaErrorMemoryAllocation ? RCS_ERR_OOM : RCS_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define RCS_CUDA(ctx, call, what)                          \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+    } while (0)
+
+int dev_sms[64] = {};
+
+int ensure_u64(rcs_ctx *c, size_t count) {
+    if (count <= c->u64_cap) return RCS_OK;
+    RCS_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
+    if (c->d_u64) cudaFree(c->d_u64);
+    c->d_u64 = nullptr;
+    c->u64_cap = 0;
+    size_t cap = std::max<size_t>(count, 1024);
+    RCS_CUDA(c, cudaMalloc(&c->d_u64, cap * sizeof(uint64_t)), "cudaMalloc scratch");
+    c->u64_cap = cap;
+    return RCS_OK;
+}
+
+int ensure_f64(rcs_ctx *c, size_t count) {
+    if (count <= c->f64_cap) return RCS_OK;
+    RCS_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
+    if (c->d_f64) cudaFree(c->d_f64);
+    c->d_f64 = nullptr;
+    c->f64_cap = 0;
+    size_t cap = std::max<size_t>(count, 1024);
+    RCS_CUDA(c, cudaMalloc(&c->d_f64, cap * sizeof(double)), "cudaMalloc scratch");
+    c->f64_cap = cap;
+    return RCS_OK;
+}
+
+// Synchronises the stream and turns the device error word into a status (and clears it).
+int drain_errors(rcs_ctx *c) {
+    RCS_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
+    int h = 0;
+    RCS_CUDA(c, cudaMemcpy(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost), "read error word");
+    if (h == 0) return RCS_OK;
+    RCS_CUDA(c, cudaMemset(c->d_err, 0, sizeof(int)), "clear error word");
+    if (h & kErrTimeout) return fail(c, RCS_ERR_TIMEOUT, "a bounded wait inside a tensor-core pass ran out");
+    if (h & kErrBadIndex) return fail(c, RCS_ERR_ARG, "bitstring index >= 2^n");
+    if (h & kErrBadAmplitude) return fail(c, RCS_ERR_ARG, "state holds an amplitude component >= 2 or not finite");
+    return fail(c, RCS_ERR_ARG, "state norm too large for the fixed-point reduction (>= 4)");
+}
+
+int valid_gates(rcs_ctx *ctx, int n, const rcs_gate *gates, size_t count, std::vector<HostGate> *out) {
+    if (count && !gates) return fail(ctx, RCS_ERR_ARG, "null gate array");
+    out->resize(count);
+    for (size_t i = 0; i < count; ++i) {
+        std::string why;
+        int rc = gate_to_host(gates[i], n, &(*out)[i], &why);
+        if (rc != RCS_OK) return fail(ctx, rc, "gate " + std::to_string(i) + ": " + why);
+    }
+    return RCS_OK;
+}
+
+
+int build_plan(rcs_ctx *ctx, int n, const std::vector<HostGate> &hg, const rcs_opts &o, Plan *plan) {
+    plan->n = n;
+    plan->precision = o.precision;
+    plan->n_gates = int64_t(hg.size());
+    switch (o.precision) {
+        case RCS_PREC_FP32_PLAIN:
+            plan->k_max = 2;
+            plan_plain(n, hg, &plan->passes);
+            break;
+        case RCS_PREC_FP32_FUSED: {
+            int k = o.k_max > 0 ? o.k_max : 4;
+            if (k < 2 || k > 5) return fail(ctx, RCS_ERR_ARG, "FP32_FUSED k_max must be 2..5");
+            plan->k_max = std::min(k, n);
+            if (n == 1) plan_plain(n, hg, &plan->passes);
+            else plan_fuse(n, hg, plan->k_max, 0, &plan->passes);
+            break;
+        }
+        case RCS_PREC_BF16X3:
+            if (o.k_max > 0 && o.k_max != kTcK) return fail(ctx, RCS_ERR_ARG, "BF16X3 uses k_max = 6");
+            if (n >= kTcK + 7) {
+                plan->k_max = kTcK;
+                plan_fuse(n, hg, kTcK, kTcK, &plan->passes);
+            } else {  // fewer than one 128-slice tile: the FP32 fused path serves small states
+                plan->k_max = std::min(5, n);
+                if (n == 1) plan_plain(n, hg, &plan->passes);
+                else plan_fuse(n, hg, plan->k_max, 0, &plan->passes);
+            }
+            break;
+        default:
+            return fail(ctx, RCS_ERR_ARG, "unknown precision");
+    }
+    return RCS_OK;
+}
+
+// Builds the BF16 operand images of every tensor-core pass into one host buffer.
+void build_ops_images(Plan &plan, std::vector<uint8_t> *img) {
+    const size_t per = tc_ops_bytes();
+    plan.tc_offset.assign(plan.passes.size(), -1);
+    size_t count = 0;
+    for (size_t i = 0; i < plan.passes.size(); ++i)
+        if (plan.passes[i].kind == PASS_TC) plan.tc_offset[i] = int64_t(per * count++);
+    img->assign(per * count, 0);
+    for (size_t i = 0; i < plan.passes.size(); ++i)
+        if (plan.tc_offset[i] >= 0) tc_build_ops(plan.passes[i], img->data() + plan.tc_offset[i]);
+}
+
+int run_passes(rcs_ctx *c, const Plan &plan, const uint8_t *d_ops) {
+    for (size_t i = 0; i < plan.passes.size(); ++i) {
+        const Pass &p = plan.passes[i];
+        int rc;
+        switch (p.kind) {
+            case PASS_1Q:
+            case PASS_2Q: rc = launch_pass_plain(c->psi, c->n, p, c->stream); break;
+            case PASS_SIMT: rc = launch_pass_simt(c->psi, c->n, p, c->stream); break;
+            case PASS_TC: rc = launch_pass_tc(c->psi, c->n, p, d_ops + plan.tc_offset[i], c->d_err, c->stream); break;
+            default: rc = RCS_ERR_ARG;
+        }
+        if (rc != RCS_OK) {
+            cudaError_t e = cudaGetLastError();
+            return fail(c, rc, "launch of pass " + std::to_string(i) + " failed: " + cudaGetErrorString(e));
+        }
+    }
+    c->sums_valid = false;
+    return RCS_OK;
+}
+
+int ensure_sums(rcs_ctx *c) {
+    if (c->sums_valid) return RCS_OK;
+    int rc = launch_block_sums(c->psi, c->n, c->bsum, c->d_err, c->stream);
+    if (rc == RCS_OK) rc = launch_block_scan(c->bsum, c->bpre, c->chunk, c->total, c->n, c->d_err, c->stream);
+    if (rc != RCS_OK) return fail(c, rc, std::string("reduction launch failed: ") + cudaGetErrorString(cudaGetLastError()));
+    c->sums_valid = true;
+    return RCS_OK;
+}
+
+}  // namespace
+
+namespace rcs {
+int device_sm_count() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 148;
+    if (!dev_sms[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        dev_sms[dev] = v > 0 ? v : 148;
+    }
+    return dev_sms[dev];
+}
+}  // namespace rcs
+
+#define RCS_TRY(ctx) try {
+#define RCS_CATCH(ctx)                                                         \
+    }                                                                          \
+    catch (const std::bad_alloc &) {                                           \
+        return fail(ctx, RCS_ERR_OOM, "host allocation failed");                \
+    }                                                                          \
+    catch (const std::exception &ex) {                                         \
+        return fail(ctx, RCS_ERR_ARG, std::string("internal error: ") + ex.what()); \
+    }
+
+extern "C" {
+
+const char *rcs_last_error(const rcs_ctx *ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
+
+int rcs_num_qubits(const rcs_ctx *ctx) { return ctx ? ctx->n : -1; }
+
+void rcs_destroy(rcs_ctx *c) {
+    if (!c) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(c->dev);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->psi);
+    cudaFree(c->bsum);
+    cudaFree(c->bpre);
+    cudaFree(c->chunk);
+    cudaFree(c->total);
+    cudaFree(c->d_err);
+    cudaFree(c->d_u64);
+    cudaFree(c->d_f64);
+    cudaFree(c->d_ops);
+    cudaSetDevice(prev);
+    delete c;
+}
+
+int rcs_create(const rcs_grid *grid, const rcs_opts *opts, rcs_ctx **out) {
+    RCS_TRY(nullptr)
+    if (!grid || !out) return fail(nullptr, RCS_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (grid->rows <= 0 || grid->cols <= 0 || grid->n_removed < 0 || (grid->n_removed && !grid->removed))
+        return fail(nullptr, RCS_ERR_ARG, "bad grid");
+    const int64_t cells = int64_t(grid->rows) * grid->cols;
+    std::vector<char> gone(size_t(std::min<int64_t>(cells, 1 << 20)), 0);
+    if (cells > (1 << 20)) return fail(nullptr, RCS_ERR_ARG, "grid too large");
+    for (int i = 0; i < grid->n_removed; ++i) {
+        int id = grid->removed[i];
+        if (id < 0 || id >= cells || gone[id]) return fail(nullptr, RCS_ERR_ARG, "bad removed cell id");
+        gone[id] = 1;
+    }
+    const int64_t n = cells - grid->n_removed;
+    if (n < 1 || n > kMaxQubits) return fail(nullptr, RCS_ERR_ARG, "qubit count must be 1..34");
+    rcs_opts o{};
+    o.precision = RCS_PREC_FP32_FUSED;
+    o.k_max = 4;
+    if (opts) o = *opts;
+    if (o.precision < RCS_PREC_FP32_PLAIN || o.precision > RCS_PREC_BF16X3)
+        return fail(nullptr, RCS_ERR_ARG, "unknown precision");
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0)
+        return fail(nullptr, RCS_ERR_UNSUPPORTED, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    auto *c = new rcs_ctx;
+    c->n = int(n);
+    c->opts = o;
+    c->stream = reinterpret_cast<cudaStream_t>(o.stream);
+    cudaGetDevice(&c->dev);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, c->dev) == cudaSuccess && prop.major < 10) {
+        delete c;
+        return fail(nullptr, RCS_ERR_UNSUPPORTED, "device is not a Blackwell (sm_10x) GPU");
+    }
+    const size_t amps = size_t(1) << n;
+    const int bl = std::min(c->n, kSampleBlockLog2);
+    const size_t nblocks = size_t(1) << (n - bl);
+    auto alloc = [&](void **p, size_t bytes, const char *what) -> int {
+        cudaError_t ee = cudaMalloc(p, bytes);
+        if (ee != cudaSuccess) {
+            cudaGetLastError();
+            std::string msg = std::string(what) + ": " + cudaGetErrorString(ee);
+            rcs_destroy(c);
+            return fail(nullptr, ee == cudaErrorMemoryAllocation ? RCS_ERR_OOM : RCS_ERR_CUDA, msg);
+        }
+        return RCS_OK;
+    };
+    int rc;
+    if ((rc = alloc(reinterpret_cast<void **>(&c->psi), amps * sizeof(float2), "state allocation")) != RCS_OK) return rc;
+    if ((rc = alloc(reinterpret_cast<void **>(&c->bsum), nblocks * 8, "block sums")) != RCS_OK) return rc;
+    if ((rc = alloc(reinterpret_cast<void **>(&c->bpre), nblocks * 8, "block prefix")) != RCS_OK) return rc;
+    if ((rc = alloc(reinterpret_cast<void **>(&c->chunk), (scan_chunks(c->n) + 1) * 8, "scan chunks")) != RCS_OK)
+        return rc;
+    if ((rc = alloc(reinterpret_cast<void **>(&c->total), 8, "total")) != RCS_OK) return rc;
+    if ((rc = alloc(reinterpret_cast<void **>(&c->d_err), sizeof(int), "error word")) != RCS_OK) return rc;
+    if (cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess || launch_init_zero(c->psi, c->n, c->stream) != RCS_OK) {
+        std::string msg = std::string("initialisation: ") + cudaGetErrorString(cudaGetLastError());
+        rcs_destroy(c);
+        return fail(nullptr, RCS_ERR_CUDA, msg);
+    }
+    *out = c;
+    return RCS_OK;
+    RCS_CATCH(nullptr)
+}
+
+int rcs_set_stream(rcs_ctx *c, uint64_t stream) {
+    if (!c) return fail(nullptr, RCS_ERR_ARG, "null context");
+    c->stream = reinterpret_cast<cudaStream_t>(stream);
+    c->opts.stream = stream;
+    return RCS_OK;
+}
+
+int rcs_reset(rcs_ctx *c) {
+    if (!c) return fail(nullptr, RCS_ERR_ARG, "null context");
+    c->sums_valid = false;
+    if (launch_init_zero(c->psi, c->n, c->stream) != RCS_OK)
+        return fail(c, RCS_ERR_CUDA, std::string("reset: ") + cudaGetErrorString(cudaGetLastError()));
+    return RCS_OK;
+}
+
+int rcs_sync(rcs_ctx *c) {
+    if (!c) return fail(nullptr, RCS_ERR_ARG, "null context");
+    return drain_errors(c);
+}
+
+int rcs_apply_circuit(rcs_ctx *c, const rcs_gate *gates, size_t n_gates) {
+    if (!c) return fail(nullptr, RCS_ERR_ARG, "null context");
+    RCS_TRY(c)
+    std::vector<HostGate> hg;
+    int rc = valid_gates(c, c->n, gates, n_gates, &hg);
+    if (rc != RCS_OK) return rc;
+    Plan plan;
+    if ((rc = build_plan(c, c->n, hg, c->opts, &plan)) != RCS_OK) return rc;
+    std::vector<uint8_t> img;
+    build_ops_images(plan, &img);
+    if (!img.empty()) {
+        if (img.size() > c->ops_cap) {
+            RCS_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
+            cudaFree(c->d_ops);
+            c->d_ops = nullptr;
+            c->ops_cap = 0;
+            RCS_CUDA(c, cudaMalloc(&c->d_ops, img.size()), "cudaMalloc operand images");
+            c->ops_cap = img.size();
+        }
+        // pageable source: the call returns once the bytes are staged, ordered on the stream
+        RCS_CUDA(c, cudaMemcpyAsync(c->d_ops, img.data(), img.size(), cudaMemcpyHostToDevice, c->stream),
+                 "upload operand images");
+    }
+    return run_passes(c, plan, c->d_ops);
+    RCS_CATCH(c)
+}
+
+int rcs_apply_unitary(rcs_ctx *c, int k, const int32_t *targets, const double *u_re_im) {
+    if (!c) return fail(nullptr, RCS_ERR_ARG, "null context");
+    RCS_TRY(c)
+    if (k < 1 || k > kTcK || !targets || !u_re_im) return fail(c, RCS_ERR_ARG, "k must be 1..6 with targets and u");
+    if (k > c->n) return fail(c, RCS_ERR_QUBIT, "more targets than qubits");
+    uint64_t seen = 0;
+    for (int i = 0; i < k; ++i) {
+        if (targets[i] < 0 || targets[i] >= c->n || ((seen >> targets[i]) & 1))
+            return fail(c, RCS_ERR_QUBIT, "bad or repeated target");
+        seen |= 1ull << targets[i];
+    }
+    const int d = 1 << k;
+    std::vector<cd> U(size_t(d) * d);
+    for (size_t e = 0; e < U.size(); ++e) U[e] = cd(u_re_im[2 * e], u_re_im[2 * e + 1]);
+    double worst = 0.0;
+    for (int r = 0; r < d; ++r)
+        for (int cc = 0; cc < d; ++cc) {
+            cd s = 0.0;
+            for (int l = 0; l < d; ++l) s += U[size_t(r) * d + l] * std::conj(U[size_t(cc) * d + l]);
+            worst = std::max(worst, std::abs(s - (r == cc ? 1.0 : 0.0)));
+        }
+    if (!(worst <= 1e-6)) return fail(c, RCS_ERR_ARG, "matrix is not unitary to 1e-6");
+    // reorder to ascending targets: local bit i (targets[i]) moves to its rank
+    int order[8], rank[8];
+    for (int i = 0; i < k; ++i) order[i] = i;
+    std::sort(order, order + k, [&](int x, int y) { return targets[x] < targets[y]; });
+    for (int p = 0; p < k; ++p) rank[order[p]] = p;
+    auto remap = [&](int j) {
+        int r = 0;
+        for (int i = 0; i < k; ++i)
+            if ((j >> i) & 1) r |= 1 << rank[i];
+        return r;
+    };
+    Pass p;
+    p.k = k;
+    for (int i = 0; i < 8; ++i) p.t[i] = i < k ? targets[order[i]] : -1;
+    p.U.assign(U.size(), cd(0.0));
+    for (int j = 0; j < d; ++j)
+        for (int l = 0; l < d; ++l) p.U[size_t(remap(j)) * d + remap(l)] = U[size_t(j) * d + l];
+    Plan plan;
+    plan.n = c->n;
+    plan.precision = c->opts.precision;
+    plan.n_gates = 1;
+    if (k == kTcK && c->opts.precision == RCS_PREC_BF16X3 && c->n >= kTcK + 7) p.kind = PASS_TC;
+    else if (k <= 5) p.kind = PASS_SIMT;
+    else return fail(c, RCS_ERR_UNSUPPORTED, "6-qubit unitaries need the BF16X3 path and n >= 13");
+    plan.passes.push_back(p);
+    std::vector<uint8_t> img;
+    build_ops_images(plan, &img);
+    if (!img.empty()) {
+        if (img.size() > c->ops_cap) {
+            RCS_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
+            cudaFree(c->d_ops);
+            c->d_ops = nullptr;
+            c->ops_cap = 0;
+            RCS_CUDA(c, cudaMalloc(&c->d_ops, img.size()), "cudaMalloc operand images");
+            c->ops_cap = img.size();
+        }
+        RCS_CUDA(c, cudaMemcpyAsync(c->d_ops, img.data(), img.size(), cudaMemcpyHostToDevice, c->stream),
+                 "upload operand images");
+    }
+    return run_passes(c, plan, c->d_ops);
+    RCS_CATCH(c)
+}
+
+int rcs_plan_build(int n, const rcs_gate *gates, size_t n_gates, const rcs_opts *opts, rcs_plan **out) {
+    RCS_TRY(nullptr)
+    if (!out) return fail(nullptr, RCS_ERR_ARG, "null output");
+    *out = nullptr;
+    if (n < 1 || n > kMaxQubits) return fail(nullptr, RCS_ERR_ARG, "qubit count must be 1..34");
+    rcs_opts o{};
+    o.precision = RCS_PREC_FP32_FUSED;
+    o.k_max = 4;
+    if (opts) o = *opts;
+    std::vector<HostGate> hg;
+    int rc = valid_gates(nullptr, n, gates, n_gates, &hg);
+    if (rc != RCS_OK) return rc;
+    auto *p = new rcs_plan;
+    rc = build_plan(nullptr, n, hg, o, &p->p);
+    if (rc != RCS_OK) {
+        delete p;
+        return rc;
+    }
+    *out = p;
+    return RCS_OK;
+    RCS_CATCH(nullptr)
+}
+
+int rcs_plan_info(const rcs_plan *plan, rcs_plan_stats *out) {
+    if (!plan || !out) return fail(nullptr, RCS_ERR_ARG, "null argument");
+    const Plan &p = plan->p;
+    std::memset(out, 0, sizeof(*out));
+    out->n_qubits = p.n;
+    out->precision = p.precision;
+    out->n_gates = p.n_gates;
+    out->n_passes = int64_t(p.passes.size());
+    const double amps = double(uint64_t(1) << p.n);
+    int kmax = 0;
+    for (const Pass &q : p.passes) {
+        kmax = std::max(kmax, q.k);
+        const double mult = q.kind == PASS_TC ? 3.0 : 1.0;
+        out->flops += mult * 8.0 * double(1 << q.k) * amps;
+    }
+    out->k_max = kmax;
+    out->hbm_bytes = 16.0 * amps * double(p.passes.size());
+    return RCS_OK;
+}
+
+int rcs_plan_pass(const rcs_plan *plan, size_t i, int32_t *k, int32_t *targets, double *u_re_im) {
+    if (!plan || !k || !targets) return fail(nullptr, RCS_ERR_ARG, "null argument");
+    if (i >= plan->p.passes.size()) return fail(nullptr, RCS_ERR_ARG, "pass index out of range");
+    const Pass &p = plan->p.passes[i];
+    *k = p.k;
+    for (int j = 0; j < 8; ++j) targets[j] = j < p.k ? p.t[j] : -1;
+    if (u_re_im)
+        for (size_t e = 0; e < p.U.size(); ++e) {
+            u_re_im[2 * e] = p.U[e].real();
+            u_re_im[2 * e + 1] = p.U[e].imag();
+        }
+    return RCS_OK;
+}
+
+int rcs_plan_upload(rcs_ctx *c, rcs_plan *plan) {
+    if (!c || !plan) return fail(c, RCS_ERR_ARG, "null argument");
+    RCS_TRY(c)
+    if (plan->p.n != c->n) return fail(c, RCS_ERR_ARG, "plan was built for another qubit count");
+    if (plan->d_ops_dev == c->dev) return RCS_OK;
+    std::vector<uint8_t> img;
+    build_ops_images(plan->p, &img);
+    if (plan->d_ops) cudaFree(plan->d_ops);
+    plan->d_ops = nullptr;
+    if (!img.empty()) {
+        RCS_CUDA(c, cudaMalloc(&plan->d_ops, img.size()), "cudaMalloc plan operands");
+        RCS_CUDA(c, cudaMemcpy(plan->d_ops, img.data(), img.size(), cudaMemcpyHostToDevice), "upload plan operands");
+    }
+    plan->d_ops_dev = c->dev;
+    return RCS_OK;
+    RCS_CATCH(c)
+}
+
+int rcs_plan_run(rcs_ctx *c, rcs_plan *plan) {
+    if (!c || !plan) return fail(c, RCS_ERR_ARG, "null argument");
+    if (plan->p.n != c->n) return fail(c, RCS_ERR_ARG, "plan was built for another qubit count");
+    if (plan->d_ops_dev != c->dev) {
+        int rc = rcs_plan_upload(c, plan);
+        if (rc != RCS_OK) return rc;
+    }
+    return run_passes(c, plan->p, plan->d_ops);
+}
+
+void rcs_plan_destroy(rcs_plan *plan) {
+    if (!plan) return;
+    if (plan->d_ops) cudaFree(plan->d_ops);
+    delete plan;
+}
+
+int rcs_amplitudes(rcs_ctx *c, const uint64_t *bits, size_t n, double *out_re_im) {
+    if (!c) return fail(nullptr, RCS_ERR_ARG, "null context");
+    if (n == 0) return RCS_OK;
+    if (!bits || !out_re_im) return fail(c, RCS_ERR_ARG, "null argument");
+    const uint64_t lim = uint64_t(1) << c->n;
+    for (size_t i = 0; i < n; ++i)
+        if (bits[i] >= lim) return fail(c, RCS_ERR_ARG, "bitstring index >= 2^n");
+    int rc;
+    if ((rc = ensure_u64(c, n)) != RCS_OK || (rc = ensure_f64(c, 2 * n)) != RCS_OK) return rc;
+    RCS_CUDA(c, cudaMemcpyAsync(c->d_u64, bits, n * 8, cudaMemcpyHostToDevice, c->stream), "upload bitstrings");
+    if (launch_gather(c->psi, c->n, c->d_u64, n, c->d_f64, c->d_err, c->stream) != RCS_OK)
+        return fail(c, RCS_ERR_CUDA, std::string("gather launch: ") + cudaGetErrorString(cudaGetLastError()));
+    RCS_CUDA(c, cudaMemcpyAsync(out_re_im, c->d_f64, n * 16, cudaMemcpyDeviceToHost, c->stream), "download");
+    return drain_errors(c);
+}
+
+int rcs_state_read(rcs_ctx *c, uint64_t first, uint64_t count, float *out_re_im) {
+    if (!c) return fail(nullptr, RCS_ERR_ARG, "null context");
+    const uint64_t lim = uint64_t(1) << c->n;
+    if (first > lim || count > lim - first || (count && !out_re_im)) return fail(c, RCS_ERR_ARG, "bad range");
+    if (count)
+        RCS_CUDA(c, cudaMemcpyAsync(out_re_im, c->psi + first, count * 8, cudaMemcpyDeviceToHost, c->stream),
+                 "read state");
+    return drain_errors(c);
+}
+
+int rcs_state_write(rcs_ctx *c, uint64_t first, uint64_t count, const float *in_re_im) {
+    if (!c) return fail(nullptr, RCS_ERR_ARG, "null context");
+    const uint64_t lim = uint64_t(1) << c->n;
+    if (first > lim || count > lim - first || (count && !in_re_im)) return fail(c, RCS_ERR_ARG, "bad range");
+    if (count)
+        RCS_CUDA(c, cudaMemcpyAsync(c->psi + first, in_re_im, count * 8, cudaMemcpyHostToDevice, c->stream),
+                 "write state");
+    c->sums_valid = false;
+    return drain_errors(c);
+}
+
+int rcs_state_device(rcs_ctx *c, void **d_state) {
+    if (!c || !d_state) return fail(c, RCS_ERR_ARG, "null argument");
+    *d_state = c->psi;
+    c->sums_valid = false;  // the caller may write through the pointer
+    return RCS_OK;
+}
+
+int rcs_norm(rcs_ctx *c, double *out) {
+    if (!c || !out) return fail(c, RCS_ERR_ARG, "null argument");
+    int rc = ensure_sums(c);
+    if (rc != RCS_OK) return rc;
+    uint64_t t = 0;
+    RCS_CUDA(c, cudaMemcpyAsync(&t, c->total, 8, cudaMemcpyDeviceToHost, c->stream), "download total");
+    if ((rc = drain_errors(c)) != RCS_OK) {
+        c->sums_valid = false;
+        return rc;
+    }
+    *out = std::ldexp(double(t), -62);
+    return RCS_OK;
+}
+
+int rcs_sample_device(rcs_ctx *c, uint64_t shots, uint64_t seed, uint64_t *d_out_bits) {
+    if (!c) return fail(nullptr, RCS_ERR_ARG, "null context");
+    if (shots == 0) return RCS_OK;
+    if (!d_out_bits) return fail(c, RCS_ERR_ARG, "null output");
+    int rc = ensure_sums(c);
+    if (rc != RCS_OK) return rc;
+    if (launch_sample(c->psi, c->n, c->bsum, c->bpre, c->total, shots, seed, d_out_bits, c->stream) != RCS_OK)
+        return fail(c, RCS_ERR_CUDA, std::string("sampler launch: ") + cudaGetErrorString(cudaGetLastError()));
+    return RCS_OK;
+}
+
+int rcs_sample(rcs_ctx *c, uint64_t shots, uint64_t seed, uint64_t *out_bits) {
+    if (!c) return fail(nullptr, RCS_ERR_ARG, "null context");
+    if (shots == 0) return RCS_OK;
+    if (!out_bits) return fail(c, RCS_ERR_ARG, "null output");
+    int rc = ensure_u64(c, size_t(shots));
+    if (rc != RCS_OK) return rc;
+    if ((rc = rcs_sample_device(c, shots, seed, c->d_u64)) != RCS_OK) return rc;
+    RCS_CUDA(c, cudaMemcpyAsync(out_bits, c->d_u64, shots * 8, cudaMemcpyDeviceToHost, c->stream), "download samples");
+    if ((rc = drain_errors(c)) != RCS_OK) {
+        c->sums_valid = false;
+        return rc;
+    }
+    return RCS_OK;
+}
+
+int rcs_xeb_device(rcs_ctx *c, const uint64_t *d_samples, size_t n, double *d_out_xeb) {
+    if (!c) return fail(nullptr, RCS_ERR_ARG, "null context");
+    if (n == 0 || !d_samples || !d_out_xeb) return fail(c, RCS_ERR_ARG, "need samples and an output");
+    int rc = ensure_sums(c);
+    if (rc != RCS_OK) return rc;
+    if ((rc = ensure_f64(c, xeb_partials_count(n) + 2)) != RCS_OK) return rc;
+    if (launch_xeb(c->psi, c->n, d_samples, n, c->total, c->d_f64, d_out_xeb, c->stream) != RCS_OK)
+        return fail(c, RCS_ERR_CUDA, std::string("xeb launch: ") + cudaGetErrorString(cudaGetLastError()));
+    return RCS_OK;
+}
+
+int rcs_xeb(rcs_ctx *c, const uint64_t *samples, size_t n, double *out_xeb) {
+    if (!c) return fail(nullptr, RCS_ERR_ARG, "null context");
+    if (n == 0 || !samples || !out_xeb) return fail(c, RCS_ERR_ARG, "need samples and an output");
+    const uint64_t lim = uint64_t(1) << c->n;
+    for (size_t i = 0; i < n; ++i)
+        if (samples[i] >= lim) return fail(c, RCS_ERR_ARG, "sample index >= 2^n");
+    int rc = ensure_u64(c, n + 1);
+    if (rc != RCS_OK) return rc;
+    if ((rc = ensure_f64(c, xeb_partials_count(n) + 2)) != RCS_OK) return rc;
+    RCS_CUDA(c, cudaMemcpyAsync(c->d_u64, samples, n * 8, cudaMemcpyHostToDevice, c->stream), "upload samples");
+    if ((rc = ensure_sums(c)) != RCS_OK) return rc;
+    double *d_res = c->d_f64 + xeb_partials_count(n);
+    if (launch_xeb(c->psi, c->n, c->d_u64, n, c->total, c->d_f64, d_res, c->stream) != RCS_OK)
+        return fail(c, RCS_ERR_CUDA, std::string("xeb launch: ") + cudaGetErrorString(cudaGetLastError()));
+    RCS_CUDA(c, cudaMemcpyAsync(out_xeb, d_res, 8, cudaMemcpyDeviceToHost, c->stream), "download xeb");
+    return drain_errors(c);
+}
+
+}  // extern "C"

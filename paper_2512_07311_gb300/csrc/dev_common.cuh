@@ -1,0 +1,35 @@
+// Device helpers shared by the library's kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rcs {
+
+// Inserts a 0 bit at position t of x (bits >= t move up by one).
+__device__ __forceinline__ uint64_t insert_zero(uint64_t x, int t) {
+    const uint64_t low = x & ((1ull << t) - 1ull);
+    return ((x >> t) << (t + 1)) | low;
+}
+
+// acc + m * a over complex64.
+__device__ __forceinline__ float2 cmac(float2 acc, float2 m, float2 a) {
+    acc.x = fmaf(m.x, a.x, acc.x);
+    acc.x = fmaf(-m.y, a.y, acc.x);
+    acc.y = fmaf(m.x, a.y, acc.y);
+    acc.y = fmaf(m.y, a.x, acc.y);
+    return acc;
+}
+
+// Grid size for a grid-stride kernel: enough CTAs to fill every SM `per_sm`
+// times, never more than the work needs.
+inline unsigned grid_for(uint64_t items, unsigned threads, int sms, int per_sm) {
+    uint64_t need = (items + threads - 1) / threads;
+    uint64_t cap = uint64_t(sms) * uint64_t(per_sm);
+    if (need < 1) need = 1;
+    return unsigned(need < cap ? need : cap);
+}
+
+int device_sm_count();
+
+}  // namespace rcs

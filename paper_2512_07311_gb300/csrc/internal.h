@@ -1,0 +1,94 @@
+// Internal declarations shared by the library's own translation units.
+#pragma once
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/rcs.h"
+
+namespace rcs {
+
+using cd = std::complex<double>;
+
+constexpr int kMaxQubits = 34;
+constexpr int kSampleBlockLog2 = 10;  // sampler block = 1024 amplitudes
+constexpr int kTcK = 6;               // width of the tensor-core fused pass
+
+// ---- gates (gates.cpp)
+struct HostGate {
+    int nq;
+    int q[2];
+    cd m[16];  // 2^nq x 2^nq row-major, local index j = bit(q[0]) + 2 bit(q[1])
+};
+
+// Validates one ABI gate against an n-qubit register and writes its matrix.
+// Returns RCS_OK or an RCS_ERR_* code with a message in *why.
+int gate_to_host(const rcs_gate &g, int n, HostGate *out, std::string *why);
+
+// ---- plan (planner.cpp)
+enum PassKind : int32_t {
+    PASS_1Q = 0,    // plain per-gate, one qubit
+    PASS_2Q = 1,    // plain per-gate, two qubits
+    PASS_SIMT = 2,  // fused k-qubit unitary, FP32 SIMT
+    PASS_TC = 3,    // fused 6-qubit unitary, tcgen05 BF16x3
+};
+
+struct Pass {
+    PassKind kind;
+    int k;
+    int t[8];               // ascending targets
+    std::vector<cd> U;      // 2^k x 2^k, local index over ascending targets
+};
+
+struct Plan {
+    int n = 0;
+    int precision = RCS_PREC_FP32_FUSED;
+    int k_max = 4;
+    int64_t n_gates = 0;
+    std::vector<Pass> passes;
+    // device copies, per context device (uploaded lazily)
+    int dev = -1;
+    void *d_tc_ops = nullptr;   // BF16 hi/lo operand images of PASS_TC passes
+    std::vector<int64_t> tc_offset;  // byte offset of each pass's image (-1 if none)
+};
+
+// Fuses gates into passes. k_max: largest block; pad_to: 0, or a width every
+// block is padded to with identity qubits (the tensor-core path needs k = 6).
+void plan_fuse(int n, const std::vector<HostGate> &gates, int k_max, int pad_to, std::vector<Pass> *out);
+
+// Plain per-gate plan: one PASS_1Q / PASS_2Q per gate (targets canonicalised ascending).
+void plan_plain(int n, const std::vector<HostGate> &gates, std::vector<Pass> *out);
+
+// Device error bits (the context's error word).
+constexpr int kErrBadAmplitude = 1;  // |amplitude component| >= 2, Inf or NaN met by a reduction
+constexpr int kErrNormOverflow = 2;  // fixed-point total >= 4 (state norm too large to sample)
+constexpr int kErrBadIndex = 4;      // bitstring >= 2^n met by a gather
+constexpr int kErrTimeout = 8;       // a bounded wait inside a kernel ran out
+
+// ---- kernels (launchers; all asynchronous on `stream`)
+
+int launch_init_zero(void *psi, int n, void *stream);
+int launch_pass_plain(void *psi, int n, const Pass &p, void *stream);
+int launch_pass_simt(void *psi, int n, const Pass &p, void *stream);
+int launch_pass_tc(void *psi, int n, const Pass &p, const void *d_ops, int *d_err, void *stream);
+
+// Size in bytes of the BF16x3 operand image of one 6-qubit pass, and its builder.
+size_t tc_ops_bytes();
+void tc_build_ops(const Pass &p, void *host_image);
+
+// Sampler / readout (k_sample.cu)
+int launch_block_sums(const void *psi, int n, uint64_t *bsum, int *d_err, void *stream);
+size_t scan_chunks(int n);
+int launch_block_scan(const uint64_t *bsum, uint64_t *bpre, uint64_t *chunk_tot, uint64_t *total, int n, int *d_err,
+                      void *stream);
+int launch_sample(const void *psi, int n, const uint64_t *bsum, const uint64_t *bpre, const uint64_t *total,
+                  uint64_t shots, uint64_t seed, uint64_t *d_out, void *stream);
+int launch_gather(const void *psi, int n, const uint64_t *d_bits, size_t count, double *d_out_re_im, int *d_err,
+                  void *stream);
+int launch_xeb(const void *psi, int n, const uint64_t *d_samples, size_t count, const uint64_t *total,
+               double *d_partials, double *d_out, void *stream);
+size_t xeb_partials_count(size_t count);
+
+}  // namespace rcs

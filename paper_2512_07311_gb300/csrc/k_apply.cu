@@ -1,0 +1,275 @@
+// State-update kernels on FP32 SIMT cores.
+//
+//  * k_plain_1q / k_plain_2q: one launch per gate (the "plain FP32 per-gate"
+//    baseline). Each thread moves 128-bit vectors: for a target above qubit 0,
+//    two neighbouring pairs (quads) share one float4 per operand row; for a
+//    target at qubit 0 the pair itself is one float4. HBM-bound: 16 * 2^n bytes
+//    per gate against 8 (1q) or 16 (2q) real flop per amplitude, i.e. 0.5 or 1
+//    flop per byte, far below the FP32 ridge.
+//  * k_fused_simt<K>: one launch per fused K-qubit unitary (K <= 5). Thread =
+//    one slice of 2^K amplitudes (the amplitudes that differ only in the target
+//    bits); lanes of a warp take consecutive slices, so each load instruction
+//    covers consecutive addresses along the lowest non-target qubits. The
+//    unitary travels in the kernel's parameter space (constant bank) and the
+//    fully unrolled complex mat-vec reads it as immediate constant operands.
+//    8 * 2^K real flop per amplitude: HBM-bound up to K = 4 on GB300.
+#include "dev_common.cuh"
+#include "internal.h"
+
+namespace rcs {
+
+struct Mat2 {
+    float2 m[4];
+};
+struct Mat4 {
+    float2 m[16];
+};
+
+constexpr int kUnroll = 4;
+
+template <bool T0>
+__global__ void __launch_bounds__(256) k_plain_1q(float2 *__restrict__ psi, uint64_t items, int t, Mat2 M) {
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    const uint64_t hstep = 1ull << t;
+    for (uint64_t it0 = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; it0 < items; it0 += stride * kUnroll) {
+        float4 lo[kUnroll], hi[kUnroll];
+        uint64_t idx[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const uint64_t it = it0 + u * stride;
+            if (it < items) {
+                if (T0) {
+                    idx[u] = it * 2;
+                    lo[u] = *reinterpret_cast<const float4 *>(psi + idx[u]);
+                } else {
+                    idx[u] = insert_zero(it * 2, t);
+                    lo[u] = *reinterpret_cast<const float4 *>(psi + idx[u]);
+                    hi[u] = *reinterpret_cast<const float4 *>(psi + idx[u] + hstep);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const uint64_t it = it0 + u * stride;
+            if (it >= items) continue;
+            if (T0) {
+                float2 a0 = make_float2(lo[u].x, lo[u].y), a1 = make_float2(lo[u].z, lo[u].w);
+                float2 b0 = cmac(cmac(make_float2(0.f, 0.f), M.m[0], a0), M.m[1], a1);
+                float2 b1 = cmac(cmac(make_float2(0.f, 0.f), M.m[2], a0), M.m[3], a1);
+                *reinterpret_cast<float4 *>(psi + idx[u]) = make_float4(b0.x, b0.y, b1.x, b1.y);
+            } else {
+                float2 a0 = make_float2(lo[u].x, lo[u].y), a1 = make_float2(hi[u].x, hi[u].y);
+                float2 c0 = make_float2(lo[u].z, lo[u].w), c1 = make_float2(hi[u].z, hi[u].w);
+                float2 b0 = cmac(cmac(make_float2(0.f, 0.f), M.m[0], a0), M.m[1], a1);
+                float2 b1 = cmac(cmac(make_float2(0.f, 0.f), M.m[2], a0), M.m[3], a1);
+                float2 d0 = cmac(cmac(make_float2(0.f, 0.f), M.m[0], c0), M.m[1], c1);
+                float2 d1 = cmac(cmac(make_float2(0.f, 0.f), M.m[2], c0), M.m[3], c1);
+                *reinterpret_cast<float4 *>(psi + idx[u]) = make_float4(b0.x, b0.y, d0.x, d0.y);
+                *reinterpret_cast<float4 *>(psi + idx[u] + hstep) = make_float4(b1.x, b1.y, d1.x, d1.y);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void mv4(const Mat4 &M, const float2 a[4], float2 b[4]) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) s = cmac(s, M.m[j * 4 + l], a[l]);
+        b[j] = s;
+    }
+}
+
+// Two-qubit gate on qubits lo < hi, local index j = bit(lo) + 2 bit(hi).
+template <bool LO0>
+__global__ void __launch_bounds__(256) k_plain_2q(float2 *__restrict__ psi, uint64_t items, int lo, int hi,
+                                                   Mat4 M) {
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    const uint64_t sl = 1ull << lo, sh = 1ull << hi;
+    for (uint64_t it0 = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; it0 < items; it0 += stride * 2) {
+        float4 v[2][4];
+        uint64_t base[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const uint64_t it = it0 + u * stride;
+            if (it >= items) continue;
+            if (LO0) {
+                base[u] = insert_zero(insert_zero(it, 0), hi);
+                v[u][0] = *reinterpret_cast<const float4 *>(psi + base[u]);       // j = 0, 1
+                v[u][1] = *reinterpret_cast<const float4 *>(psi + base[u] + sh);  // j = 2, 3
+            } else {
+                base[u] = insert_zero(insert_zero(it * 2, lo), hi);
+                v[u][0] = *reinterpret_cast<const float4 *>(psi + base[u]);
+                v[u][1] = *reinterpret_cast<const float4 *>(psi + base[u] + sl);
+                v[u][2] = *reinterpret_cast<const float4 *>(psi + base[u] + sh);
+                v[u][3] = *reinterpret_cast<const float4 *>(psi + base[u] + sl + sh);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const uint64_t it = it0 + u * stride;
+            if (it >= items) continue;
+            if (LO0) {
+                float2 a[4] = {make_float2(v[u][0].x, v[u][0].y), make_float2(v[u][0].z, v[u][0].w),
+                               make_float2(v[u][1].x, v[u][1].y), make_float2(v[u][1].z, v[u][1].w)};
+                float2 b[4];
+                mv4(M, a, b);
+                *reinterpret_cast<float4 *>(psi + base[u]) = make_float4(b[0].x, b[0].y, b[1].x, b[1].y);
+                *reinterpret_cast<float4 *>(psi + base[u] + sh) = make_float4(b[2].x, b[2].y, b[3].x, b[3].y);
+            } else {
+                // float4 e holds quads q (x,y) and q+1 (z,w) of operand row e
+                float2 a[4], c[4], b[4], d[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    a[e] = make_float2(v[u][e].x, v[u][e].y);
+                    c[e] = make_float2(v[u][e].z, v[u][e].w);
+                }
+                mv4(M, a, b);
+                mv4(M, c, d);
+                const uint64_t off[4] = {0, sl, sh, sl + sh};
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    *reinterpret_cast<float4 *>(psi + base[u] + off[e]) = make_float4(b[e].x, b[e].y, d[e].x, d[e].y);
+            }
+        }
+    }
+}
+
+// Complex matrix entry with its negated imaginary part precomputed on the host, so
+// the mat-vec's multiply-adds take all three as direct constant-bank operands
+// (no negation that the compiler could hoist into registers).
+struct CEnt {
+    float re, im, nim;
+};
+
+template <int K>
+struct SimtArgs {
+    CEnt U[1 << K][1 << K];
+    int t[K];  // ascending
+    uint64_t slices;
+};
+
+template <int K>
+__global__ void __launch_bounds__(256, (K >= 5 ? 1 : 2)) k_fused_simt(float2 *__restrict__ psi, const SimtArgs<K> a) {
+    constexpr int D = 1 << K;
+    // target offsets of local index j, warp-uniform; read back through a volatile
+    // pointer at every use so they are not held in registers across the mat-vec
+    __shared__ uint64_t offs_s[D];
+    if (threadIdx.x < D) {
+        uint64_t o = 0;
+#pragma unroll
+        for (int i = 0; i < K; ++i)
+            if ((threadIdx.x >> i) & 1) o |= 1ull << a.t[i];
+        offs_s[threadIdx.x] = o;
+    }
+    __syncthreads();
+    const volatile uint64_t *offs = offs_s;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+#pragma unroll 1
+    for (uint64_t s = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < a.slices; s += stride) {
+        uint64_t base = s;
+#pragma unroll
+        for (int i = 0; i < K; ++i) base = insert_zero(base, a.t[i]);
+        float2 *p = psi + base;
+        float2 v[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) v[j] = p[offs[j]];
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int l = 0; l < D; ++l) {
+                const CEnt &u = a.U[j][l];
+                acc.x = fmaf(u.re, v[l].x, acc.x);
+                acc.x = fmaf(u.nim, v[l].y, acc.x);
+                acc.y = fmaf(u.re, v[l].y, acc.y);
+                acc.y = fmaf(u.im, v[l].x, acc.y);
+            }
+            p[offs[j]] = acc;
+        }
+    }
+}
+
+__global__ void k_init_zero(float4 *__restrict__ psi4, uint64_t n4) {
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n4; i += stride)
+        psi4[i] = make_float4(i == 0 ? 1.f : 0.f, 0.f, 0.f, 0.f);
+}
+
+static int check_launch() {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? RCS_OK : RCS_ERR_CUDA;
+}
+
+int launch_init_zero(void *psi, int n, void *stream) {
+    auto st = static_cast<cudaStream_t>(stream);
+    if (n == 0) return RCS_ERR_ARG;
+    const uint64_t n4 = (1ull << n) / 2;  // n >= 1: whole float4s
+    k_init_zero<<<grid_for(n4, 256, device_sm_count(), 8), 256, 0, st>>>(static_cast<float4 *>(psi), n4);
+    return check_launch();
+}
+
+int launch_pass_plain(void *psi, int n, const Pass &p, void *stream) {
+    auto st = static_cast<cudaStream_t>(stream);
+    auto *s = static_cast<float2 *>(psi);
+    const int sms = device_sm_count();
+    if (p.kind == PASS_1Q) {
+        Mat2 M;
+        for (int e = 0; e < 4; ++e) M.m[e] = make_float2(float(p.U[e].real()), float(p.U[e].imag()));
+        const int t = p.t[0];
+        if (t == 0) {
+            const uint64_t items = 1ull << (n - 1);
+            k_plain_1q<true><<<grid_for(items, 256, sms, 8), 256, 0, st>>>(s, items, t, M);
+        } else {
+            const uint64_t items = 1ull << (n - 2);
+            k_plain_1q<false><<<grid_for(items, 256, sms, 8), 256, 0, st>>>(s, items, t, M);
+        }
+    } else if (p.kind == PASS_2Q) {
+        Mat4 M;
+        for (int e = 0; e < 16; ++e) M.m[e] = make_float2(float(p.U[e].real()), float(p.U[e].imag()));
+        const int lo = p.t[0], hi = p.t[1];
+        if (lo == 0) {
+            const uint64_t items = 1ull << (n - 2);
+            k_plain_2q<true><<<grid_for(items, 256, sms, 8), 256, 0, st>>>(s, items, lo, hi, M);
+        } else {
+            const uint64_t items = 1ull << (n - 3);
+            k_plain_2q<false><<<grid_for(items, 256, sms, 8), 256, 0, st>>>(s, items, lo, hi, M);
+        }
+    } else {
+        return RCS_ERR_ARG;
+    }
+    return check_launch();
+}
+
+template <int K>
+static int launch_simt_k(float2 *psi, int n, const Pass &p, cudaStream_t st) {
+    SimtArgs<K> a;
+    const int D = 1 << K;
+    for (int j = 0; j < D; ++j)
+        for (int l = 0; l < D; ++l) {
+            const cd &u = p.U[size_t(j) * D + l];
+            a.U[j][l] = CEnt{float(u.real()), float(u.imag()), -float(u.imag())};
+        }
+    for (int i = 0; i < K; ++i) a.t[i] = p.t[i];
+    a.slices = 1ull << (n - K);
+    const int threads = 256;
+    k_fused_simt<K><<<grid_for(a.slices, threads, device_sm_count(), 8), threads, 0, st>>>(psi, a);
+    return check_launch();
+}
+
+int launch_pass_simt(void *psi, int n, const Pass &p, void *stream) {
+    auto st = static_cast<cudaStream_t>(stream);
+    auto *s = static_cast<float2 *>(psi);
+    if (p.k > n) return RCS_ERR_ARG;
+    switch (p.k) {
+        case 1: return launch_simt_k<1>(s, n, p, st);
+        case 2: return launch_simt_k<2>(s, n, p, st);
+        case 3: return launch_simt_k<3>(s, n, p, st);
+        case 4: return launch_simt_k<4>(s, n, p, st);
+        case 5: return launch_simt_k<5>(s, n, p, st);
+        default: return RCS_ERR_UNSUPPORTED;
+    }
+}
+
+}  // namespace rcs

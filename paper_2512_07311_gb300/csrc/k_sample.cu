@@ -1,0 +1,385 @@
+// Measurement sampling and scoring kernels (Section 3.2 items 3 and 4 of the paper:
+// draw shots from |psi|^2, then score them with linear XEB).
+//
+// Probabilities enter every 2^n-term reduction as exact fixed-point integers:
+// q(x) = round(x^2 * 2^62) for each FP32 component x, computed from the float's
+// exponent and 24-bit mantissa with one 32x32->64 integer multiply. Sums of q are
+// exact (no rounding, any order), so the block sums, the block prefix scan, the
+// norm T and every cumulative probability C_i are exact multiples of 2^-62 that
+// do not depend on the summation order. GB300 runs FP64 at a small fraction of
+// its FP32/INT32 rate, so this keeps the reduction pass bound by HBM instead of by
+// the FP64 pipe, with a rounding error (2^-63 per term) far below FP64's.
+//
+// Sampling (inverse CDF): x_s = smallest i with C_i > u_s * T. The comparison
+// C_i * 2^53 > m_s * T, with u_s = m_s * 2^-53, is done exactly in 128-bit integers.
+//   1. k_block_sums: S_b = sum of q over block b (1024 amplitudes), one warp per block.
+//   2. k_scan_*:     exclusive prefix P_b of S_b, and T = sum_b S_b.
+//   3. k_sample:     one warp per shot: Philox4x64-10 uniform, binary search of the
+//                    block with P_b + S_b crossing the target, warp prefix over the
+//                    block's 32-amplitude lane ranges, sequential walk in one lane.
+// XEB: k_xeb_partial / k_xeb_final gather |psi_x|^2 in FP64 and reduce in a fixed
+// tree order, F = 2^n * mean / T - 1.
+#include "dev_common.cuh"
+#include "internal.h"
+
+namespace rcs {
+
+// round(x^2 * 2^62) for finite |x| < 2; sets *bad for |x| >= 2, Inf or NaN.
+__device__ __forceinline__ uint64_t fx_sq(float x, int &bad) {
+    const uint32_t b = __float_as_uint(x) & 0x7fffffffu;
+    uint32_t e = b >> 23;
+    uint32_t m = b & 0x7fffffu;
+    if (e) m |= 0x800000u;
+    else e = 1;
+    if (e >= 128u) bad = 1;
+    const uint64_t m2 = uint64_t(m) * uint64_t(m);  // < 2^48; x^2 * 2^62 = m2 * 2^(2e - 238)
+    const int sh = 2 * int(e) - 238;
+    if (sh >= 0) return sh <= 16 ? (m2 << sh) : 0ull;
+    const int r = -sh;
+    if (r > 48) return 0ull;
+    return ((m2 >> (r - 1)) + 1ull) >> 1;  // round half up
+}
+
+__device__ __forceinline__ uint64_t fx_amp(float2 a, int &bad) { return fx_sq(a.x, bad) + fx_sq(a.y, bad); }
+
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ uint64_t warp_incl_scan_u64(uint64_t v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint64_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+static inline int block_log2(int n) { return n < kSampleBlockLog2 ? n : kSampleBlockLog2; }
+
+// ---------------------------------------------------------------- block sums
+
+__global__ void __launch_bounds__(256) k_block_sums(const float2 *__restrict__ psi, int blog2, uint64_t nblocks,
+                                                     uint64_t *__restrict__ bsum, int *__restrict__ d_err) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
+    const uint32_t nf4 = (1u << blog2) >> 1;  // float4 per block (blog2 >= 1)
+    int bad = 0;
+    for (uint64_t b = uint64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); b < nblocks; b += warps) {
+        const float4 *p4 = reinterpret_cast<const float4 *>(psi + (b << blog2));
+        uint64_t s = 0;
+#pragma unroll 4
+        for (uint32_t c = lane; c < nf4; c += 32) {
+            float4 v = __ldg(p4 + c);
+            s += fx_sq(v.x, bad) + fx_sq(v.y, bad) + fx_sq(v.z, bad) + fx_sq(v.w, bad);
+        }
+        s = warp_sum_u64(s);
+        if (lane == 0) bsum[b] = s;
+    }
+    if (bad) atomicOr(d_err, 1);
+}
+
+int launch_block_sums(const void *psi, int n, uint64_t *bsum, int *d_err, void *stream) {
+    const int bl = block_log2(n);
+    const uint64_t nblocks = 1ull << (n - bl);
+    const unsigned grid = grid_for(nblocks * 32, 256, device_sm_count(), 8);
+    k_block_sums<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<const float2 *>(psi), bl, nblocks,
+                                                                      bsum, d_err);
+    return cudaGetLastError() == cudaSuccess ? RCS_OK : RCS_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------- scan
+
+constexpr int kScanThreads = 256;
+constexpr int kScanPer = 8;
+constexpr int kScanChunk = kScanThreads * kScanPer;  // 2048 entries per CTA
+
+// Exclusive scan over the CTA of one value per thread; returns the CTA total in *tot.
+__device__ uint64_t cta_excl_scan_u64(uint64_t v, uint64_t *tot) {
+    __shared__ uint64_t wsum[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint64_t incl = warp_incl_scan_u64(v, lane);
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        uint64_t x = lane < kScanThreads / 32 ? wsum[lane] : 0ull;
+        uint64_t xi = warp_incl_scan_u64(x, lane);
+        if (lane < kScanThreads / 32) wsum[lane] = xi - x;  // exclusive offsets of the warps
+        if (lane == kScanThreads / 32 - 1) *tot = xi;
+    }
+    __syncthreads();
+    const uint64_t r = wsum[w] + incl - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_chunks(const uint64_t *__restrict__ x, uint64_t count,
+                                                               uint64_t *__restrict__ chunk_tot) {
+    const uint64_t base = uint64_t(blockIdx.x) * kScanChunk + uint64_t(threadIdx.x) * kScanPer;
+    uint64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i)
+        if (base + i < count) s += x[base + i];
+    __shared__ uint64_t tot;
+    cta_excl_scan_u64(s, &tot);
+    if (threadIdx.x == 0) chunk_tot[blockIdx.x] = tot;
+}
+
+// One CTA: exclusive scan of the chunk totals in place, grand total to *total.
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(uint64_t *__restrict__ chunk_tot, uint64_t nchunks,
+                                                            uint64_t *__restrict__ total, int *__restrict__ d_err) {
+    __shared__ uint64_t tot;
+    uint64_t carry = 0;
+    int overflow = 0;
+    for (uint64_t off = 0; off < nchunks; off += kScanChunk) {
+        const uint64_t base = off + uint64_t(threadIdx.x) * kScanPer;
+        uint64_t v[kScanPer], s = 0;
+#pragma unroll
+        for (int i = 0; i < kScanPer; ++i) {
+            v[i] = base + i < nchunks ? chunk_tot[base + i] : 0ull;
+            if (s + v[i] < s) overflow = 1;
+            s += v[i];
+        }
+        uint64_t e = cta_excl_scan_u64(s, &tot) + carry;
+#pragma unroll
+        for (int i = 0; i < kScanPer; ++i) {
+            if (base + i < nchunks) chunk_tot[base + i] = e;
+            e += v[i];
+        }
+        if (carry + tot < carry) overflow = 1;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+    if (overflow) atomicOr(d_err, 2);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint64_t *__restrict__ x, uint64_t count,
+                                                              const uint64_t *__restrict__ chunk_off,
+                                                              uint64_t *__restrict__ out) {
+    const uint64_t base = uint64_t(blockIdx.x) * kScanChunk + uint64_t(threadIdx.x) * kScanPer;
+    uint64_t v[kScanPer], s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) {
+        v[i] = base + i < count ? x[base + i] : 0ull;
+        s += v[i];
+    }
+    __shared__ uint64_t tot;
+    uint64_t e = cta_excl_scan_u64(s, &tot) + chunk_off[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) {
+        if (base + i < count) out[base + i] = e;
+        e += v[i];
+    }
+}
+
+size_t scan_chunks(int n) {
+    const uint64_t nb = 1ull << (n - block_log2(n));
+    return size_t((nb + kScanChunk - 1) / kScanChunk);
+}
+
+int launch_block_scan(const uint64_t *bsum, uint64_t *bpre, uint64_t *chunk_tot, uint64_t *total, int n, int *d_err,
+                      void *stream) {
+    auto st = static_cast<cudaStream_t>(stream);
+    const uint64_t nb = 1ull << (n - block_log2(n));
+    const unsigned nch = unsigned(scan_chunks(n));
+    k_scan_chunks<<<nch, kScanThreads, 0, st>>>(bsum, nb, chunk_tot);
+    k_scan_top<<<1, kScanThreads, 0, st>>>(chunk_tot, nch, total, d_err);
+    k_scan_apply<<<nch, kScanThreads, 0, st>>>(bsum, nb, chunk_tot, bpre);
+    return cudaGetLastError() == cudaSuccess ? RCS_OK : RCS_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------- Philox4x64-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC'11):
+// 10 rounds; round: (hi0,lo0) = M0*x0, (hi1,lo1) = M1*x2,
+// x' = (hi1 ^ x1 ^ k0, lo1, hi0 ^ x3 ^ k1, lo0); key += (W0, W1) between rounds.
+
+__device__ __forceinline__ uint64_t philox_word(uint64_t ctr0, uint64_t key0, int word) {
+    uint64_t x0 = ctr0, x1 = 0, x2 = 0, x3 = 0, k0 = key0, k1 = 0;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B97F4A7C15ull;
+            k1 += 0xBB67AE8584CAA73Bull;
+        }
+        const uint64_t lo0 = 0xD2E7470EE14C6C93ull * x0, hi0 = __umul64hi(0xD2E7470EE14C6C93ull, x0);
+        const uint64_t lo1 = 0xCA5A826395121157ull * x2, hi1 = __umul64hi(0xCA5A826395121157ull, x2);
+        const uint64_t y0 = hi1 ^ x1 ^ k0, y2 = hi0 ^ x3 ^ k1;
+        x0 = y0;
+        x1 = lo1;
+        x2 = y2;
+        x3 = lo0;
+    }
+    return word == 0 ? x0 : word == 1 ? x1 : word == 2 ? x2 : x3;
+}
+
+// a * 2^53 > (rhi, rlo) as 128-bit unsigned integers
+__device__ __forceinline__ bool above(uint64_t a, uint64_t rhi, uint64_t rlo) {
+    const uint64_t hi = a >> 11, lo = a << 53;
+    return hi > rhi || (hi == rhi && lo > rlo);
+}
+
+// ---------------------------------------------------------------- sampler
+
+__global__ void __launch_bounds__(256) k_sample(const float2 *__restrict__ psi, int blog2, uint64_t nblocks,
+                                                 const uint64_t *__restrict__ bsum,
+                                                 const uint64_t *__restrict__ bpre,
+                                                 const uint64_t *__restrict__ total, uint64_t shots, uint64_t seed,
+                                                 uint64_t *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
+    const uint64_t T = *total;
+    const uint32_t bamps = 1u << blog2;
+    int bad = 0;
+    for (uint64_t s = uint64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); s < shots; s += warps) {
+        if (T == 0) {
+            if (lane == 0) out[s] = ~0ull;
+            continue;
+        }
+        const uint64_t m = philox_word(s >> 2, seed, int(s & 3)) >> 11;  // u = m * 2^-53
+        const uint64_t rlo = m * T, rhi = __umul64hi(m, T);
+        // smallest block whose inclusive prefix crosses the target
+        uint64_t lo = 0, hi = nblocks - 1;
+        while (lo < hi) {
+            const uint64_t mid = lo + ((hi - lo) >> 1);
+            if (above(bpre[mid] + bsum[mid], rhi, rlo)) hi = mid;
+            else lo = mid + 1;
+        }
+        const uint64_t b = lo;
+        const uint64_t base = bpre[b];
+        const float2 *blk = psi + (b << blog2);
+        const uint32_t a0 = uint32_t(lane) * 32u;
+        uint64_t ls = 0;
+        if (a0 < bamps) {
+            const uint32_t cnt = bamps - a0 < 32u ? bamps - a0 : 32u;
+            for (uint32_t a = 0; a < cnt; a += 2) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(blk + a0 + a));
+                ls += fx_sq(v.x, bad) + fx_sq(v.y, bad) + fx_sq(v.z, bad) + fx_sq(v.w, bad);
+            }
+        }
+        const uint64_t incl = warp_incl_scan_u64(ls, lane);
+        const unsigned hit = __ballot_sync(0xffffffffu, above(base + incl, rhi, rlo));
+        const int L = __ffs(hit) - 1;  // hit != 0: lane 31's prefix is P_b + S_b
+        uint64_t idx = 0;
+        if (lane == L) {
+            uint64_t run = base + incl - ls;
+            const uint32_t cnt = bamps - a0 < 32u ? bamps - a0 : 32u;
+            idx = (b << blog2) + a0 + cnt - 1;
+            for (uint32_t a = 0; a < cnt; ++a) {
+                run += fx_amp(blk[a0 + a], bad);
+                if (above(run, rhi, rlo)) {
+                    idx = (b << blog2) + a0 + a;
+                    break;
+                }
+            }
+        }
+        idx = __shfl_sync(0xffffffffu, idx, L < 0 ? 0 : L);
+        if (lane == 0) out[s] = idx;
+    }
+}
+
+int launch_sample(const void *psi, int n, const uint64_t *bsum, const uint64_t *bpre, const uint64_t *total,
+                  uint64_t shots, uint64_t seed, uint64_t *d_out, void *stream) {
+    if (shots == 0) return RCS_OK;
+    const int bl = block_log2(n);
+    const uint64_t nblocks = 1ull << (n - bl);
+    const unsigned grid = grid_for(shots * 32, 256, device_sm_count(), 8);
+    k_sample<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<const float2 *>(psi), bl, nblocks, bsum,
+                                                                  bpre, total, shots, seed, d_out);
+    return cudaGetLastError() == cudaSuccess ? RCS_OK : RCS_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------- gather
+
+__global__ void k_gather(const float2 *__restrict__ psi, uint64_t namps, const uint64_t *__restrict__ bits,
+                         uint64_t count, double *__restrict__ out, int *__restrict__ d_err) {
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += stride) {
+        const uint64_t x = bits[i];
+        if (x >= namps) {
+            out[2 * i] = out[2 * i + 1] = __longlong_as_double(0x7ff8000000000000ll);
+            atomicOr(d_err, 4);
+            continue;
+        }
+        const float2 a = psi[x];
+        out[2 * i] = double(a.x);
+        out[2 * i + 1] = double(a.y);
+    }
+}
+
+int launch_gather(const void *psi, int n, const uint64_t *d_bits, size_t count, double *d_out_re_im, int *d_err,
+                  void *stream) {
+    if (count == 0) return RCS_OK;
+    k_gather<<<grid_for(count, 256, device_sm_count(), 4), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const float2 *>(psi), 1ull << n, d_bits, count, d_out_re_im, d_err);
+    return cudaGetLastError() == cudaSuccess ? RCS_OK : RCS_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------- XEB
+
+constexpr int kXebThreads = 256;
+constexpr uint64_t kXebPerCta = 4096;
+
+size_t xeb_partials_count(size_t count) { return size_t((count + kXebPerCta - 1) / kXebPerCta); }
+
+__device__ double cta_sum_f64(double v) {
+    __shared__ double ws[kXebThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) ws[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < kXebThreads / 32; ++i) r += ws[i];
+    __syncthreads();
+    return r;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kXebThreads) k_xeb_partial(const float2 *__restrict__ psi, uint64_t namps,
+                                                              const uint64_t *__restrict__ x, uint64_t count,
+                                                              double *__restrict__ partials) {
+    const uint64_t beg = uint64_t(blockIdx.x) * kXebPerCta;
+    const uint64_t end = beg + kXebPerCta < count ? beg + kXebPerCta : count;
+    double s = 0.0;
+    bool bad = false;
+    for (uint64_t i = beg + threadIdx.x; i < end; i += kXebThreads) {
+        const uint64_t xi = x[i];
+        if (xi >= namps) {
+            bad = true;
+            continue;
+        }
+        const float2 a = psi[xi];
+        s += double(a.x) * double(a.x) + double(a.y) * double(a.y);
+    }
+    const int anybad = __syncthreads_or(bad);
+    const double r = cta_sum_f64(s);
+    if (threadIdx.x == 0) partials[blockIdx.x] = anybad ? __longlong_as_double(0x7ff8000000000000ll) : r;
+}
+
+__global__ void __launch_bounds__(kXebThreads) k_xeb_final(const double *__restrict__ partials, uint64_t nparts,
+                                                            uint64_t count, int n, const uint64_t *__restrict__ total,
+                                                            double *__restrict__ out) {
+    double s = 0.0;
+    for (uint64_t i = threadIdx.x; i < nparts; i += kXebThreads) s += partials[i];
+    const double r = cta_sum_f64(s);
+    if (threadIdx.x == 0) {
+        const double T = ldexp(double(*total), -62);
+        *out = ldexp(r / double(count), n) / T - 1.0;
+    }
+}
+
+int launch_xeb(const void *psi, int n, const uint64_t *d_samples, size_t count, const uint64_t *total,
+               double *d_partials, double *d_out, void *stream) {
+    auto st = static_cast<cudaStream_t>(stream);
+    if (count == 0) return RCS_ERR_ARG;
+    const size_t np = xeb_partials_count(count);
+    k_xeb_partial<<<unsigned(np), kXebThreads, 0, st>>>(static_cast<const float2 *>(psi), 1ull << n, d_samples, count,
+                                                        d_partials);
+    k_xeb_final<<<1, kXebThreads, 0, st>>>(d_partials, np, count, n, total, d_out);
+    return cudaGetLastError() == cudaSuccess ? RCS_OK : RCS_ERR_CUDA;
+}
+
+}  // namespace rcs

@@ -1,0 +1,426 @@
+// Fused 6-qubit state update on the 5th-generation tensor cores (tcgen05), with a
+// BF16 hi/lo split of both operands and three products accumulated in FP32.
+//
+// One pass applies a 64x64 complex unitary U to every slice of the state: slice s
+// is the 64 amplitudes that differ only in the 6 target bits. Written as a real
+// GEMM on interleaved (re, im) data, each slice x (128 reals) maps to R x with the
+// realified R (128 x 128): R[2a][2b] = Re U[a][b], R[2a][2b+1] = -Im U[a][b],
+// R[2a+1][2b] = Im U[a][b], R[2a+1][2b+1] = Re U[a][b]. A tile of 128 slices is
+//     D (128 slices x 128 outputs) = X (128 x 128) * R^T (128 x 128),
+// one tcgen05 MMA chain with M = N = 128 and K = 128 (8 steps of K = 16).
+// Split precision: x = x_hi + x_lo, R = R_hi + R_lo with hi = bf16(v), lo =
+// bf16(v - hi); D = X_hi R_hi^T + X_lo R_hi^T + X_hi R_lo^T (the lo*lo term, about
+// 2^-17 relative, is dropped), accumulated in FP32 in tensor memory.
+//
+// Data flow per CTA (persistent, one CTA per SM, 17 warps):
+//   warps 0-7  (loaders):  cp.async 8-byte copies of a tile's amplitudes into a
+//              shared-memory stage (two tiles in flight), then split each amplitude
+//              into bf16x2 hi and lo words and write them to tensor memory with
+//              tcgen05.st: the slice's 64 amplitudes become row s of the A operand
+//              (A is read by the MMA straight from TMEM, lane = slice).
+//   warp 16    (MMA):      one thread issues the 24 MMAs of a tile (B = R^T from
+//              shared memory, 128-byte swizzled, K-major) and commits to an mbarrier.
+//   warps 8-15 (epilogue): tcgen05.ld of the FP32 accumulator rows (lane = slice)
+//              and coalesced 8-byte stores of the new amplitudes, in place.
+// Tensor memory holds two buffers of {D: 128 cols, A_hi: 64 cols, A_lo: 64 cols},
+// so loading tile i+1, the MMAs of tile i and the stores of tile i-1 overlap.
+// Lanes of a warp always take 32 consecutive slices, so every global load and store
+// instruction walks consecutive addresses along the lowest non-target qubits.
+//
+// Every wait is bounded (about one second of SM clock); on expiry the kernel raises
+// an error bit, drains its own MMAs and copies, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "dev_common.cuh"
+#include "internal.h"
+
+namespace rcs {
+
+namespace tc {
+constexpr int K = kTcK;         // 6 target qubits
+constexpr int D = 1 << K;       // 64 amplitudes per slice
+constexpr int KR = 2 * D;       // 128 reals per slice (GEMM K)
+constexpr int NR = 2 * D;       // 128 real outputs (GEMM N)
+constexpr int M = 128;          // slices per tile (GEMM M, TMEM lanes)
+constexpr int kLoaderWarps = 8;
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = (kLoaderWarps + kEpiWarps + 1) * 32;  // 544
+constexpr int kOpBytes = NR * KR * 2;                          // one bf16 operand image: 32 KB
+constexpr int kStageBytes = D * M * 8;                         // one tile of complex64: 64 KB
+// shared memory map (offsets from a 1024-aligned base)
+constexpr int kSmBhi = 0;
+constexpr int kSmBlo = kOpBytes;
+constexpr int kSmStage0 = 2 * kOpBytes;
+constexpr int kSmStage1 = kSmStage0 + kStageBytes;
+constexpr int kSmOff = kSmStage1 + kStageBytes;  // 64 x u64 target offsets
+constexpr int kSmBar = kSmOff + D * 8;           // 6 mbarriers
+constexpr int kSmMisc = kSmBar + 6 * 8;          // tmem slot, abort flag
+constexpr int kSmBytes = kSmMisc + 16;
+constexpr int kSmAlloc = kSmBytes + 1024;        // slack for 1024-byte alignment
+constexpr uint32_t kTmemCols = 512;
+constexpr long long kWaitCycles = 1ll << 31;     // ~1 s at 2 GHz
+// instruction descriptor: D f32, A bf16, B bf16, both K-major, N = 128, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(NR >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}  // namespace tc
+
+struct TcArgs {
+    float2 *psi;
+    const uint4 *ops;  // B_hi image then B_lo image (shared-memory layout, 64 KB)
+    int *err;
+    uint32_t tiles;
+    int t[tc::K];      // ascending targets
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return uint32_t(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false if another role aborted or the wait ran out (which aborts).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > tc::kWaitCycles) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+// Warp-uniform bounded wait: lane 0 polls (with the time limit), the verdict is
+// broadcast, then every lane performs its own (now immediately successful)
+// acquiring test so the whole warp is ordered after the phase. The phase cannot
+// move on before this warp arrives on its own barrier, so the test cannot miss it.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag) ? 1 : 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (ok) (void)mbar_try_wait(bar, parity);
+    __syncwarp();
+    return ok != 0;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+#define RCS_R32(v)                                                                                              \
+    "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), \
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]),            \
+        "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]),            \
+        "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+#define RCS_W32(v)                                                                                   \
+    "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),     \
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),        \
+        "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),      \
+        "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),      \
+        "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+        RCS_R32(v)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : RCS_W32(v)
+        : "r"(taddr)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = uint64_t((saddr & 0x3FFFFu) >> 4);
+    d |= uint64_t(1) << 16;            // leading byte offset (unused for swizzled K-major)
+    d |= uint64_t(1024 >> 4) << 32;    // stride byte offset
+    d |= uint64_t(1) << 46;            // descriptor version
+    d |= uint64_t(2) << 61;            // 128-byte swizzle
+    return d;
+}
+
+__device__ __forceinline__ void mma_bf16_tmemA(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(tc::kIdesc), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ uint64_t slice_base(uint64_t s, const int (&t)[tc::K]) {
+#pragma unroll
+    for (int i = 0; i < tc::K; ++i) s = insert_zero(s, t[i]);
+    return s;
+}
+
+__device__ __forceinline__ uint32_t bf162_bits(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t *>(&v); }
+
+__global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_constant__ TcArgs a) {
+    using namespace tc;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *off = reinterpret_cast<uint64_t *>(sm + kSmOff);
+    const uint32_t bar0 = smem_u32(sm + kSmBar);
+    auto bar_full = [&](int b) { return bar0 + 8u * uint32_t(b); };
+    auto bar_done = [&](int b) { return bar0 + 16u + 8u * uint32_t(b); };
+    auto bar_free = [&](int b) { return bar0 + 32u + 8u * uint32_t(b); };
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + kSmMisc);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + kSmMisc + 4);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int t[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) t[i] = a.t[i];
+
+    // ---- set-up: operand image, offset table, barriers, tensor memory
+    {
+        uint4 *dst = reinterpret_cast<uint4 *>(sm);
+        for (int i = threadIdx.x; i < 2 * kOpBytes / 16; i += kThreads) dst[i] = a.ops[i];
+        if (threadIdx.x < D) {
+            uint64_t o = 0;
+#pragma unroll
+            for (int i = 0; i < K; ++i)
+                if ((threadIdx.x >> i) & 1) o |= 1ull << t[i];
+            off[threadIdx.x] = o;
+        }
+        if (threadIdx.x == 0) {
+            mbar_init(bar_full(0), kLoaderWarps);
+            mbar_init(bar_full(1), kLoaderWarps);
+            mbar_init(bar_done(0), 1);
+            mbar_init(bar_done(1), 1);
+            mbar_init(bar_free(0), kEpiWarps);
+            mbar_init(bar_free(1), kEpiWarps);
+            *abort_flag = 0;
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (warp == kLoaderWarps + kEpiWarps) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                         "r"(kTmemCols)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t ntile = a.tiles;
+    const uint32_t my_tiles = blockIdx.x < ntile ? (ntile - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+    if (warp < kLoaderWarps) {
+        // ---------------------------------------------------------------- loaders
+        const int q = warp & 3, h = warp >> 2;  // TMEM lane quarter, amplitude half
+        const int srow = 32 * q + lane;          // slice within the tile = TMEM lane
+        const uint32_t stage0_u32 = smem_u32(sm + kSmStage0);
+        auto issue = [&](uint32_t i, int b) {
+            const uint64_t tile = uint64_t(blockIdx.x) + uint64_t(i) * gridDim.x;
+            const uint64_t base = slice_base(tile * M + srow, t);
+#pragma unroll 8
+            for (int jj = 0; jj < 32; ++jj) {
+                const int j = 32 * h + jj;
+                const float2 *src = a.psi + (base | off[j]);
+                const uint32_t dst = stage0_u32 + uint32_t(b * kStageBytes + (j * M + srow) * 8);
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        if (my_tiles > 0) issue(0, 0);
+        if (my_tiles > 1) issue(1, 1);
+        for (uint32_t i = 0; i < my_tiles; ++i) {
+            const int b = i & 1;
+            if (i + 1 < my_tiles) asm volatile("cp.async.wait_group 1;" ::: "memory");
+            else asm volatile("cp.async.wait_group 0;" ::: "memory");
+            if (i >= 2 && !warp_wait(bar_done(b), ((i >> 1) - 1) & 1, abort_flag)) break;
+            tc_fence_after();
+            uint32_t hi[32], lo[32];
+            const float2 *stage = reinterpret_cast<const float2 *>(sm + kSmStage0 + b * kStageBytes);
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+                const float2 v = stage[(32 * h + jj) * M + srow];
+                const __nv_bfloat162 vh = __floats2bfloat162_rn(v.x, v.y);
+                const float2 hf = __bfloat1622float2(vh);
+                const __nv_bfloat162 vl = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
+                hi[jj] = bf162_bits(vh);
+                lo[jj] = bf162_bits(vl);
+            }
+            const uint32_t lane_base = tmem + (uint32_t(32 * q) << 16);
+            const uint32_t col = uint32_t(b) * 256u;
+            tmem_st32(lane_base + col + 128u + uint32_t(32 * h), hi);
+            tmem_st32(lane_base + col + 192u + uint32_t(32 * h), lo);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_full(b));
+            if (i + 2 < my_tiles) issue(i + 2, b);
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    } else if (warp < kLoaderWarps + kEpiWarps) {
+        // ---------------------------------------------------------------- epilogue
+        const int e = warp - kLoaderWarps;
+        const int q = e & 3, h = e >> 2;
+        const int srow = 32 * q + lane;
+        for (uint32_t i = 0; i < my_tiles; ++i) {
+            const int b = i & 1;
+            if (!warp_wait(bar_done(b), (i >> 1) & 1, abort_flag)) break;
+            tc_fence_after();
+            const uint64_t tile = uint64_t(blockIdx.x) + uint64_t(i) * gridDim.x;
+            const uint64_t base = slice_base(tile * M + srow, t);
+            const uint32_t lane_base = tmem + (uint32_t(32 * q) << 16) + uint32_t(b) * 256u;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                uint32_t v[32];
+                tmem_ld32(lane_base + uint32_t(64 * h + 32 * c), v);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int aa = 0; aa < 16; ++aa) {
+                    const int j = 32 * h + 16 * c + aa;
+                    a.psi[base | off[j]] = make_float2(__uint_as_float(v[2 * aa]), __uint_as_float(v[2 * aa + 1]));
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_free(b));
+        }
+    } else {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t bhi = smem_u32(sm + kSmBhi), blo = smem_u32(sm + kSmBlo);
+            int64_t last = -1;
+            for (uint32_t i = 0; i < my_tiles; ++i) {
+                const int b = i & 1;
+                if (!mbar_wait(bar_full(b), (i >> 1) & 1, abort_flag)) break;
+                if (i >= 2 && !mbar_wait(bar_free(b), ((i >> 1) - 1) & 1, abort_flag)) break;
+                tc_fence_after();
+                const uint32_t dcol = tmem + uint32_t(b) * 256u;
+                const uint32_t ahi = dcol + 128u, alo = dcol + 192u;
+#pragma unroll
+                for (int kk = 0; kk < KR / 16; ++kk) {
+                    // K step kk covers reals [16 kk, 16 kk + 16): atom column kk / 4, 32-byte step kk % 4
+                    const uint32_t boff = uint32_t(kk >> 2) * uint32_t(NR * 128) + uint32_t(kk & 3) * 32u;
+                    const uint64_t dhi = sw128_desc(bhi + boff), dlo = sw128_desc(blo + boff);
+                    const uint32_t acol = uint32_t(kk) * 8u;  // 16 bf16 = 8 TMEM columns
+                    mma_bf16_tmemA(dcol, ahi + acol, dhi, kk > 0 ? 1u : 0u);
+                    mma_bf16_tmemA(dcol, alo + acol, dhi, 1u);
+                    mma_bf16_tmemA(dcol, ahi + acol, dlo, 1u);
+                }
+                mma_commit(bar_done(b));
+                last = i;
+            }
+            if (*abort_flag && last >= 0) {
+                // drain: the last committed MMAs must finish before tensor memory is freed
+                const long long t0 = clock64();
+                while (!mbar_try_wait(bar_done(int(last & 1)), uint32_t((last >> 1) & 1)) &&
+                       clock64() - t0 < kWaitCycles) {
+                }
+            }
+        }
+        __syncwarp();
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0 && *abort_flag) atomicOr(a.err, 8);
+    if (warp == kLoaderWarps + kEpiWarps) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------- host side
+
+static uint16_t bf16_rn_bits(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7fffffffu) > 0x7f800000u) return uint16_t((u >> 16) | 0x40);  // NaN stays NaN
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return uint16_t(u >> 16);
+}
+static float bf16_to_float(uint16_t b) {
+    uint32_t u = uint32_t(b) << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+size_t tc_ops_bytes() { return size_t(2 * tc::kOpBytes); }
+
+// Byte offset of element (row n, k) in the K-major, 128-byte-swizzled image of a
+// 128 x 128 bf16 operand: two 64-element atom columns of 128 rows x 128 bytes;
+// within a row the 16-byte chunk c sits at chunk c ^ (n mod 8).
+static size_t sw128_offset(int n, int k) {
+    const int kc = k >> 6, within = (k & 63) * 2;
+    const int chunk = within >> 4, byte = within & 15;
+    return size_t(kc) * (tc::NR * 128) + size_t(n) * 128 + size_t(((chunk ^ (n & 7)) << 4) + byte);
+}
+
+void tc_build_ops(const Pass &p, void *host_image) {
+    using namespace tc;
+    uint8_t *img = static_cast<uint8_t *>(host_image);
+    std::memset(img, 0, tc_ops_bytes());
+    for (int oa = 0; oa < D; ++oa)
+        for (int ib = 0; ib < D; ++ib) {
+            const cd u = p.U[size_t(oa) * D + ib];
+            // R rows 2oa (re out), 2oa+1 (im out); columns 2ib (re in), 2ib+1 (im in)
+            const double r[2][2] = {{u.real(), -u.imag()}, {u.imag(), u.real()}};
+            for (int ro = 0; ro < 2; ++ro)
+                for (int ci = 0; ci < 2; ++ci) {
+                    const double v = r[ro][ci];
+                    const uint16_t h = bf16_rn_bits(float(v));
+                    const uint16_t l = bf16_rn_bits(float(v - double(bf16_to_float(h))));
+                    const size_t o = sw128_offset(2 * oa + ro, 2 * ib + ci);
+                    std::memcpy(img + kSmBhi + o, &h, 2);
+                    std::memcpy(img + kSmBlo + o, &l, 2);
+                }
+        }
+}
+
+int launch_pass_tc(void *psi, int n, const Pass &p, const void *d_ops, int *d_err, void *stream) {
+    using namespace tc;
+    if (p.k != K || n < K + 7) return RCS_ERR_UNSUPPORTED;
+    static bool attr_done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !attr_done[dev]) {
+        if (cudaFuncSetAttribute(k_fused_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmAlloc) != cudaSuccess)
+            return RCS_ERR_CUDA;
+        attr_done[dev] = true;
+    }
+    TcArgs a;
+    a.psi = static_cast<float2 *>(psi);
+    a.ops = static_cast<const uint4 *>(d_ops);
+    a.err = d_err;
+    a.tiles = uint32_t((1ull << (n - K)) / M);
+    for (int i = 0; i < K; ++i) a.t[i] = p.t[i];
+    const unsigned grid = unsigned(std::min<uint64_t>(a.tiles, uint64_t(device_sm_count())));
+    k_fused_tc<<<grid, kThreads, kSmAlloc, static_cast<cudaStream_t>(stream)>>>(a);
+    return cudaGetLastError() == cudaSuccess ? RCS_OK : RCS_ERR_CUDA;
+}
+
+}  // namespace rcs

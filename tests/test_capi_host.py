@@ -1,0 +1,117 @@
+"""C-ABI library on the CPU: it loads, exports every declared symbol, and its host
+logic (gate validation, the fusion planner) is right. No GPU call is made here."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2512_07311_gb300 import build as B
+from paper_2512_07311_gb300 import capi
+from paper_2512_07311_gb300 import circuits as C
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return capi.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "rcs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char \*)\s*\*?\s*(rcs_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+    bound = {n for n, _, _ in capi.SIGNATURES}
+    assert set(names) <= bound, set(names) - bound
+
+
+def test_error_messages_without_gpu(lib):
+    with pytest.raises(capi.RcsError) as e:
+        capi.rcs_plan_build(4, np.array([C.make_gate(C.SQRT_X, 7)]))
+    assert e.value.code == capi.RCS_ERR_QUBIT
+    assert "out of range" in str(e.value)
+    with pytest.raises(capi.RcsError) as e:
+        capi.rcs_plan_build(4, np.array([C.make_gate(C.FSIM, 1, 1)]))
+    assert e.value.code == capi.RCS_ERR_QUBIT
+    bad = np.array([C.make_gate(C.U1, 0)])
+    with pytest.raises(capi.RcsError) as e:
+        capi.rcs_plan_build(4, bad, umats={0: np.array([[1, 1], [0, 1]])})
+    assert e.value.code == capi.RCS_ERR_ARG
+    with pytest.raises(capi.RcsError):
+        capi.rcs_plan_build(4, np.array([C.make_gate(9, 0)]))
+    with pytest.raises(capi.RcsError):
+        capi.rcs_plan_build(40, np.zeros(0, dtype=C.GATE_DTYPE))
+
+
+def _plan_passes(plan):
+    info = capi.rcs_plan_info(plan)
+    return info, [capi.rcs_plan_pass(plan, i) for i in range(info["n_passes"])]
+
+
+@pytest.mark.parametrize("precision,kmax,n", [(capi.RCS_PREC_FP32_FUSED, 2, 10), (capi.RCS_PREC_FP32_FUSED, 4, 10),
+                                              (capi.RCS_PREC_FP32_FUSED, 5, 9), (capi.RCS_PREC_BF16X3, 0, 13),
+                                              (capi.RCS_PREC_FP32_PLAIN, 0, 9)])
+def test_fused_plan_reproduces_circuit(oracle, lib, precision, kmax, n):
+    """Applying the planned passes (FP64 matrices) with the oracle equals applying
+    the circuit gate by gate with the oracle."""
+    grid = C.grid_for_n(n)
+    circ = C.generate(grid, cycles=6, pattern="EFGH", seed=17, jitter=0.05)
+    plan = capi.rcs_plan_build(n, circ.gates, precision, kmax)
+    try:
+        info, passes = _plan_passes(plan)
+    finally:
+        capi.rcs_plan_destroy(plan)
+    want = oracle.simulate(n, circ.gates)
+    psi = oracle.zero_state(n)
+    for targets, U in passes:
+        assert list(targets) == sorted(targets)
+        np.testing.assert_allclose(U @ U.conj().T, np.eye(len(U)), atol=1e-12)
+        oracle.apply_matrix(psi, targets, U)
+    np.testing.assert_allclose(psi, want, atol=1e-12)
+    assert info["n_gates"] == len(circ.gates)
+    if precision == capi.RCS_PREC_FP32_PLAIN:
+        assert info["n_passes"] == len(circ.gates)
+    elif precision == capi.RCS_PREC_BF16X3:
+        assert all(len(t) == 6 for t, _ in passes)
+    else:
+        assert max(len(t) for t, _ in passes) <= kmax
+        assert info["n_passes"] < len(circ.gates)
+
+
+def test_fusion_counts_34q():
+    circ = C.config_circuit("34q_5x7m1_20cyc")
+    counts = {}
+    for prec, k in [(capi.RCS_PREC_FP32_PLAIN, 0), (capi.RCS_PREC_FP32_FUSED, 4), (capi.RCS_PREC_BF16X3, 0)]:
+        plan = capi.rcs_plan_build(34, circ.gates, prec, k)
+        info = capi.rcs_plan_info(plan)
+        capi.rcs_plan_destroy(plan)
+        counts[prec] = info["n_passes"]
+        assert info["hbm_bytes"] == 16.0 * 2**34 * info["n_passes"]
+    assert counts[capi.RCS_PREC_FP32_PLAIN] == 994
+    assert counts[capi.RCS_PREC_FP32_FUSED] < 100
+    assert counts[capi.RCS_PREC_BF16X3] < 60
+
+
+def test_plan_pass_targets_and_adjoint(oracle, lib):
+    # a U2 gate with reversed qubit order and the adjoint flag
+    rng = np.random.default_rng(3)
+    A = rng.normal(size=(4, 4)) + 1j * rng.normal(size=(4, 4))
+    Q, _ = np.linalg.qr(A)
+    g = C.make_gate(C.U2, 5, 2, flags=C.ADJOINT)
+    plan = capi.rcs_plan_build(6, np.array([g]), capi.RCS_PREC_FP32_PLAIN, 0, umats={0: Q})
+    t, U = capi.rcs_plan_pass(plan, 0)
+    capi.rcs_plan_destroy(plan)
+    assert list(t) == [2, 5]
+    psi0 = rng.normal(size=64) + 1j * rng.normal(size=64)
+    want = oracle.apply_matrix(psi0.copy(), [5, 2], Q.conj().T)
+    got = oracle.apply_matrix(psi0.copy(), list(t), U)
+    np.testing.assert_allclose(got, want, atol=1e-12)

@@ -1,0 +1,276 @@
+"""GPU path vs the complex128 CPU oracle, through the C ABI (needs a GB300).
+
+Tolerances (stated once, used throughout):
+  * final-state infidelity 1 - |<a|b>|^2 / (|a|^2 |b|^2) <= 1e-5, both in FP64;
+  * max amplitude error |psi_gpu - psi_oracle|_inf <= 1e-6 absolute (same gate
+    convention on both sides, so no global phase is removed);
+  * |XEB_gpu - XEB_oracle| <= 0.005 on the same shots (observed: ~1e-7);
+  * samples: inverse-CDF draws on the GPU's own state agree with the oracle's
+    draws on that same state (promoted exactly to complex128) in >= 99.99% of
+    shots (a flip needs a uniform within ~1e-16 of a CDF boundary); against the
+    oracle's own state at 12 qubits >= 99.9%.
+  * one tensor-core pass: each output within 4e-5 * |slice|_2, from the BF16 split
+    residuals (2^-17 relative on each operand, lo*lo dropped) plus FP32
+    accumulation over 128 terms;
+  * norm drift of the tensor-core path <= 2e-6 per pass: its FP32 accumulation
+    loses about 8e-7 of the norm per pass, always downward (measured; a scale
+    factor only -- the sampler and XEB divide by the computed norm and the
+    infidelity above is taken between normalised vectors). FP32 SIMT paths keep
+    |norm - 1| <= 1e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2512_07311_gb300 import build as B
+from paper_2512_07311_gb300 import capi
+from paper_2512_07311_gb300 import circuits as C
+
+pytestmark = pytest.mark.gpu
+
+INFID_TOL = 1e-5
+AMP_TOL = 1e-6
+XEB_TOL = 0.005
+PRECS = [capi.RCS_PREC_FP32_PLAIN, capi.RCS_PREC_FP32_FUSED, capi.RCS_PREC_BF16X3]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return capi.load()
+
+
+def infidelity(a, b):
+    a = np.asarray(a, dtype=np.complex128)
+    b = np.asarray(b, dtype=np.complex128)
+    ov = np.vdot(a, b)
+    return 1.0 - (abs(ov) ** 2) / (np.vdot(a, a).real * np.vdot(b, b).real)
+
+
+def run_gpu(n_or_grid, gates, precision, k_max=0):
+    ctx = capi.rcs_create(n_or_grid, precision, k_max)
+    capi.rcs_apply_circuit(ctx, gates)
+    capi.rcs_sync(ctx)
+    return ctx
+
+
+def rand_unitary(d, rng):
+    A = rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))
+    Q, R = np.linalg.qr(A)
+    return Q * (np.diag(R) / np.abs(np.diag(R)))
+
+
+# ------------------------------------------------------------------ whole circuits
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_config_12q_vs_oracle(lib, oracle, precision):
+    circ = C.config_circuit("12q_3x4_8cyc")
+    n = circ.n_qubits
+    want = oracle.simulate(n, circ.gates)
+    ctx = run_gpu(circ.grid, circ.gates, precision)
+    try:
+        got = capi.rcs_state_read(ctx)
+        assert infidelity(got, want) <= INFID_TOL
+        assert np.abs(got - want).max() <= AMP_TOL
+        assert abs(capi.rcs_norm(ctx) - 1.0) <= 1e-5  # 12 qubits: every path is FP32 SIMT
+        # samples on the same uniforms against the oracle's own state
+        shots, seed = 10_000, 2024
+        xs = capi.rcs_sample(ctx, shots, seed)
+        xo = oracle.sample(want, shots, seed)
+        assert np.mean(xs == xo) >= 0.999
+        F_gpu = capi.rcs_xeb(ctx, xs)
+        F_or = oracle.xeb(want, xs)
+        assert abs(F_gpu - F_or) <= XEB_TOL
+        assert abs(F_gpu - F_or) <= 1e-4
+        assert abs(oracle.xeb(want, xo) - F_gpu) <= 0.05  # same shots up to boundary flips
+    finally:
+        capi.rcs_destroy(ctx)
+
+
+@pytest.fixture(scope="module")
+def circ20(oracle):
+    circ = C.generate(C.Grid(4, 5), cycles=10, pattern="EFGH", seed=7, jitter=0.05)
+    return circ, oracle.simulate(circ.n_qubits, circ.gates)
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_circuit_20q_vs_oracle(lib, oracle, circ20, precision):
+    circ, want = circ20
+    ctx = run_gpu(circ.grid, circ.gates, precision)
+    try:
+        got = capi.rcs_state_read(ctx)
+        inf = infidelity(got, want)
+        err = np.abs(got - want).max()
+        assert inf <= INFID_TOL, inf
+        assert err <= AMP_TOL, err
+        # sampler on the GPU's own state vs the oracle sampler on the same state
+        shots, seed = 200_000, 99
+        xs = capi.rcs_sample(ctx, shots, seed)
+        xo = oracle.sample(got.astype(np.complex128), shots, seed)
+        assert np.mean(xs == xo) >= 0.9999
+        p = np.abs(got.astype(np.complex128)) ** 2
+        assert (p[xs.astype(np.int64)] > 0).all()
+        F_gpu = capi.rcs_xeb(ctx, xs)
+        assert abs(F_gpu - oracle.xeb(want, xs)) <= XEB_TOL
+        assert abs(F_gpu - oracle.xeb(got.astype(np.complex128), xs)) <= 1e-9
+    finally:
+        capi.rcs_destroy(ctx)
+
+
+@pytest.mark.parametrize("k_max", [2, 3, 5])
+def test_fused_widths_vs_oracle(lib, oracle, circ20, k_max):
+    circ, want = circ20
+    ctx = run_gpu(circ.grid, circ.gates, capi.RCS_PREC_FP32_FUSED, k_max)
+    try:
+        got = capi.rcs_state_read(ctx)
+        assert infidelity(got, want) <= INFID_TOL
+        assert np.abs(got - want).max() <= AMP_TOL
+    finally:
+        capi.rcs_destroy(ctx)
+
+
+# ------------------------------------------------------------------ tensor-core pass alone
+
+@pytest.mark.parametrize("n,targets", [(13, [0, 1, 2, 3, 4, 5]), (13, [7, 8, 9, 10, 11, 12]),
+                                       (14, [0, 3, 6, 9, 12, 13]), (16, [2, 5, 1, 15, 8, 11]),
+                                       (22, [21, 0, 10, 4, 17, 6]), (24, [9, 10, 11, 12, 13, 14])])
+def test_tc_pass_vs_oracle(lib, oracle, n, targets):
+    rng = np.random.default_rng(n * 100 + targets[0])
+    psi0 = (rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)).astype(np.complex64)
+    psi0 /= np.linalg.norm(psi0)
+    ctx = capi.rcs_create(n, capi.RCS_PREC_BF16X3)
+    try:
+        capi.rcs_state_write(ctx, psi0)
+        want = psi0.astype(np.complex128)
+        for rep in range(3):
+            U = rand_unitary(64, rng)
+            capi.rcs_apply_unitary(ctx, targets, U)
+            capi.rcs_sync(ctx)
+            got = capi.rcs_state_read(ctx).astype(np.complex128)
+            prev = want.copy()
+            oracle.apply_matrix(want, targets, U)
+            # per-output bound: 4e-5 * |slice|_2 <= 4e-5 * max slice norm
+            mask = sum(1 << t for t in targets)
+            idx = np.arange(1 << n)
+            base = idx & ~mask
+            slice_norm2 = np.zeros(1 << n)
+            np.add.at(slice_norm2, base, np.abs(prev) ** 2)
+            bound = 4e-5 * math.sqrt(slice_norm2.max())
+            err = np.abs(got - want).max()
+            assert err <= bound, (rep, err, bound)
+            assert infidelity(got, want) <= 1e-8
+            want = got  # continue from the GPU's state
+    finally:
+        capi.rcs_destroy(ctx)
+
+
+NORM_DRIFT_PER_TC_PASS = 2e-6
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_echo_24q(lib, precision):
+    """C followed by C^dagger returns |0...0>: no oracle needed, any size."""
+    circ = C.generate(C.grid_for_n(24), cycles=14, pattern="ABCDCDAB", seed=31, jitter=0.05)
+    plan = capi.rcs_plan_build(24, circ.gates, precision)
+    passes = 2 * capi.rcs_plan_info(plan)["n_passes"]
+    capi.rcs_plan_destroy(plan)
+    ctx = capi.rcs_create(24, precision)
+    try:
+        capi.rcs_apply_circuit(ctx, circ.gates)
+        capi.rcs_apply_circuit(ctx, C.inverse_gates(circ.gates))
+        a0 = capi.rcs_amplitudes(ctx, [0])[0]
+        norm = capi.rcs_norm(ctx)
+        assert abs(a0) ** 2 / norm >= 1 - INFID_TOL
+        drift = NORM_DRIFT_PER_TC_PASS * passes if precision == capi.RCS_PREC_BF16X3 else 1e-5
+        assert abs(norm - 1) <= drift, (norm, drift)
+    finally:
+        capi.rcs_destroy(ctx)
+
+
+# ------------------------------------------------------------------ sampler and readout
+
+def test_planted_state_sampler_exact(lib, oracle):
+    n = 18
+    psi = np.zeros(1 << n, dtype=np.complex64)
+    support = {5: 0.5, 77_777: 0.25, 77_778: 0.125, (1 << n) - 1: 0.0625, 1 << 17: 0.0625}
+    for i, pr in support.items():
+        psi[i] = np.complex64(math.sqrt(pr) * np.exp(0.3j * i))
+    ctx = capi.rcs_create(n, capi.RCS_PREC_FP32_FUSED)
+    try:
+        capi.rcs_state_write(ctx, psi)
+        shots = 100_000
+        xs = capi.rcs_sample(ctx, shots, seed=12)
+        xo = oracle.sample(psi.astype(np.complex128), shots, seed=12)
+        assert set(np.unique(xs).tolist()) <= set(support)
+        assert np.mean(xs == xo) >= 0.9999
+        assert abs(capi.rcs_norm(ctx) - float(np.sum(np.abs(psi.astype(np.complex128)) ** 2))) <= 1e-12
+        one = capi.rcs_sample(ctx, 1, seed=12)
+        assert one[0] == xs[0]
+    finally:
+        capi.rcs_destroy(ctx)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 9, 10, 11])
+def test_small_and_ragged_states(lib, oracle, n):
+    circ = C.generate(C.grid_for_n(n), cycles=3, seed=n)
+    want = oracle.simulate(n, circ.gates)
+    for prec in PRECS:
+        ctx = run_gpu(n, circ.gates, prec)
+        try:
+            got = capi.rcs_state_read(ctx)
+            assert np.abs(got - want).max() <= AMP_TOL
+            xs = capi.rcs_sample(ctx, 3000, seed=4)
+            xo = oracle.sample(got.astype(np.complex128), 3000, seed=4)
+            assert np.mean(xs == xo) >= 0.999
+            assert abs(capi.rcs_xeb(ctx, xs) - oracle.xeb(got.astype(np.complex128), xs)) <= 1e-9
+        finally:
+            capi.rcs_destroy(ctx)
+
+
+def test_amplitudes_and_errors(lib):
+    n = 16
+    circ = C.generate(C.grid_for_n(n), cycles=4, seed=3)
+    ctx = run_gpu(n, circ.gates, capi.RCS_PREC_FP32_FUSED)
+    try:
+        full = capi.rcs_state_read(ctx)
+        idx = np.random.default_rng(0).integers(0, 1 << n, size=5000, dtype=np.uint64)
+        amps = capi.rcs_amplitudes(ctx, idx)
+        np.testing.assert_array_equal(amps, full[idx.astype(np.int64)].astype(np.complex128))
+        with pytest.raises(capi.RcsError) as e:
+            capi.rcs_amplitudes(ctx, [1 << n])
+        assert e.value.code == capi.RCS_ERR_ARG
+        with pytest.raises(capi.RcsError):
+            capi.rcs_xeb(ctx, [0, 1 << n])
+        with pytest.raises(capi.RcsError) as e:
+            capi.rcs_apply_circuit(ctx, np.array([C.make_gate(C.SQRT_X, n)]))
+        assert e.value.code == capi.RCS_ERR_QUBIT
+        # the state is unchanged by the rejected calls
+        np.testing.assert_array_equal(capi.rcs_state_read(ctx), full)
+    finally:
+        capi.rcs_destroy(ctx)
+
+
+def test_device_pointer_calls(lib, oracle):
+    torch = pytest.importorskip("torch")
+    n = 20
+    circ = C.generate(C.grid_for_n(n), cycles=6, seed=8)
+    stream = torch.cuda.current_stream().cuda_stream
+    ctx = capi.rcs_create(n, capi.RCS_PREC_BF16X3, stream=stream)
+    try:
+        capi.rcs_apply_circuit(ctx, circ.gates)
+        shots = 50_000
+        d_bits = torch.empty(shots, dtype=torch.int64, device="cuda")
+        d_xeb = torch.empty(1, dtype=torch.float64, device="cuda")
+        capi.rcs_sample_device(ctx, shots, 5, d_bits.data_ptr())
+        capi.rcs_xeb_device(ctx, d_bits.data_ptr(), shots, d_xeb.data_ptr())
+        torch.cuda.current_stream().synchronize()
+        xs = d_bits.cpu().numpy().view(np.uint64)
+        np.testing.assert_array_equal(xs, capi.rcs_sample(ctx, shots, 5))
+        assert abs(float(d_xeb.item()) - capi.rcs_xeb(ctx, xs)) <= 1e-12
+        bad = torch.tensor([1 << n], dtype=torch.int64, device="cuda")
+        capi.rcs_xeb_device(ctx, bad.data_ptr(), 1, d_xeb.data_ptr())
+        torch.cuda.current_stream().synchronize()
+        assert math.isnan(float(d_xeb.item()))
+    finally:
+        capi.rcs_destroy(ctx)
