@@ -40,6 +40,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(C.CONFIGS))
     ap.add_argument("--shots", type=int, default=None)
+    ap.add_argument("--qubits", type=int, default=None,
+                    help="profiling size: a circuit of the same family (20 cycles, ABCDCDAB) on a grid of this "
+                         "many qubits instead of the named workload")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP32 plain/fused comparison runs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     return ap.parse_args()
@@ -198,7 +201,11 @@ def main():
     B.build()
     capi.load()
     cfg = C.CONFIGS[args.workload]
-    circ = C.config_circuit(args.workload)
+    if args.qubits:
+        circ = C.generate(C.grid_for_n(args.qubits), 20, "ABCDCDAB", seed=2)
+        args.workload = f"{args.qubits}q_profile_20cyc"
+    else:
+        circ = C.config_circuit(args.workload)
     n = circ.n_qubits
     shots = args.shots or cfg["shots"]
     stream = torch.cuda.current_stream()
@@ -332,7 +339,8 @@ def main():
             "config": {"workload": args.workload, "qubits": n, "cycles": circ.cycles, "pattern": circ.pattern,
                        "grid": f"{circ.grid.rows}x{circ.grid.cols}-{len(circ.grid.removed)}", "shots": shots,
                        "gates": len(circ.gates), "passes": passes, "precision": "bf16x3",
-                       "state_bytes": 8 * 2**n, "l2": "inputs larger than L2 (state 128 GiB)",
+                       "state_bytes": 8 * 2**n, "l2": (f"inputs larger than L2 (state {8 * 2**n / 2**30:.0f} GiB > 129 MB)" if 8 * 2**n > 129e6
+                              else "state fits in L2: no flush between steps"),
                        "parallelism": f"replicas{world}" if world > 1 else "single"},
             "shots_per_s": shots / (statistics.median(sample_ms) / 1e3),
             "phases_ms": {"reset+apply": statistics.median(apply_ms), "sample": statistics.median(sample_ms),
