@@ -224,6 +224,31 @@ int rcs_xeb(rcs_ctx *ctx, const uint64_t *samples, size_t n, double *out_xeb);
  * An out-of-range sample makes the result NaN. */
 int rcs_xeb_device(rcs_ctx *ctx, const uint64_t *d_samples, size_t n, double *d_out_xeb);
 
+/* ------------------------------------------------------------------ allocation-free scoring */
+
+/* Linear XEB, as rcs_xeb_device, for callers that cannot allocate device memory:
+ * no context is needed and no cudaMalloc, cudaFree or allocating library routine
+ * is called. (The paper has no counterpart; this serves callers such as code
+ * running while a stream is captured into a CUDA graph, where cudaMalloc is not
+ * allowed, or hosts whose device memory comes only from their own arena.)
+ *
+ * d_state: DEVICE, 2^n_qubits complex64 amplitudes (interleaved re, im);
+ * d_samples: DEVICE, count uint64 basis indices; d_out_xeb: DEVICE, one double;
+ * stream: cudaStream_t (0 = legacy default stream). Work is enqueued on the
+ * stream and the call returns; an index >= 2^n or an unusable state makes the
+ * result NaN.
+ *
+ * Scratch lives in one fixed 192 KiB device array inside this library, which
+ * every GPU that loads the library holds until the process exits. Hence:
+ * count <= 67108864 (2^26) and 1 <= n_qubits <= 34, else RCS_ERR_ARG with a
+ * message for rcs_last_error(NULL). The first call on a device looks up the
+ * array's device address (with that device current); make that first call
+ * before any stream capture. Every call shares the array: calls whose work
+ * overlaps on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller. */
+int rcs_xeb_static(const void *d_state, int n_qubits, const uint64_t *d_samples, size_t count, double *d_out_xeb,
+                   uint64_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -77,6 +77,8 @@ SIGNATURES = [
     ("rcs_sample_device", ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p]),
     ("rcs_xeb", ctypes.c_int, [_P, _u64p, ctypes.c_size_t, _f64p]),
     ("rcs_xeb_device", ctypes.c_int, [_P, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("rcs_xeb_static", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
+                                      ctypes.c_void_p, ctypes.c_uint64]),
 ]
 
 _lib = None
@@ -269,3 +271,8 @@ def rcs_xeb(ctx, samples) -> float:
 
 def rcs_xeb_device(ctx, d_samples: int, n: int, d_out: int):
     _check(load().rcs_xeb_device(ctx, d_samples, n, d_out), ctx)
+
+
+def rcs_xeb_static(d_state: int, n_qubits: int, d_samples: int, count: int, d_out: int, stream: int = 0):
+    """Allocation-free XEB on caller-owned device buffers (see include/rcs.h)."""
+    _check(load().rcs_xeb_static(d_state, n_qubits, d_samples, count, d_out, stream))

@@ -189,6 +189,11 @@ int ensure_sums(rcs_ctx *c) {
 }  // namespace
 
 namespace rcs {
+int set_thread_error(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
 int device_sm_count() {
     int dev = 0;
     cudaGetDevice(&dev);

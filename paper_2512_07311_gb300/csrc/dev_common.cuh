@@ -21,6 +21,23 @@ __device__ __forceinline__ float2 cmac(float2 acc, float2 m, float2 a) {
     return acc;
 }
 
+// round(x^2 * 2^62) for finite |x| < 2, exactly (from the float's exponent and
+// 24-bit mantissa, one 32x32->64 multiply); sets bad for |x| >= 2, Inf or NaN.
+__device__ __forceinline__ uint64_t fx_sq(float x, int &bad) {
+    const uint32_t b = __float_as_uint(x) & 0x7fffffffu;
+    uint32_t e = b >> 23;
+    uint32_t m = b & 0x7fffffu;
+    if (e) m |= 0x800000u;
+    else e = 1;
+    if (e >= 128u) bad = 1;
+    const uint64_t m2 = uint64_t(m) * uint64_t(m);  // < 2^48; x^2 * 2^62 = m2 * 2^(2e - 238)
+    const int sh = 2 * int(e) - 238;
+    if (sh >= 0) return sh <= 16 ? (m2 << sh) : 0ull;
+    const int r = -sh;
+    if (r > 48) return 0ull;
+    return ((m2 >> (r - 1)) + 1ull) >> 1;  // round half up
+}
+
 // Grid size for a grid-stride kernel: enough CTAs to fill every SM `per_sm`
 // times, never more than the work needs.
 inline unsigned grid_for(uint64_t items, unsigned threads, int sms, int per_sm) {

@@ -16,6 +16,9 @@ constexpr int kMaxQubits = 34;
 constexpr int kSampleBlockLog2 = 10;  // sampler block = 1024 amplitudes
 constexpr int kTcK = 6;               // width of the tensor-core fused pass
 
+// Records msg as the calling thread's last error (rcs_last_error(NULL)); returns code.
+int set_thread_error(int code, const std::string &msg);
+
 // ---- gates (gates.cpp)
 struct HostGate {
     int nq;

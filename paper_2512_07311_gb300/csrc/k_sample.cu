@@ -24,22 +24,6 @@
 
 namespace rcs {
 
-// round(x^2 * 2^62) for finite |x| < 2; sets *bad for |x| >= 2, Inf or NaN.
-__device__ __forceinline__ uint64_t fx_sq(float x, int &bad) {
-    const uint32_t b = __float_as_uint(x) & 0x7fffffffu;
-    uint32_t e = b >> 23;
-    uint32_t m = b & 0x7fffffu;
-    if (e) m |= 0x800000u;
-    else e = 1;
-    if (e >= 128u) bad = 1;
-    const uint64_t m2 = uint64_t(m) * uint64_t(m);  // < 2^48; x^2 * 2^62 = m2 * 2^(2e - 238)
-    const int sh = 2 * int(e) - 238;
-    if (sh >= 0) return sh <= 16 ? (m2 << sh) : 0ull;
-    const int r = -sh;
-    if (r > 48) return 0ull;
-    return ((m2 >> (r - 1)) + 1ull) >> 1;  // round half up
-}
-
 __device__ __forceinline__ uint64_t fx_amp(float2 a, int &bad) { return fx_sq(a.x, bad) + fx_sq(a.y, bad); }
 
 __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
