@@ -29,6 +29,10 @@ sys.path.insert(0, ROOT)
 from paper_2512_07311_gb300 import circuits as C  # noqa: E402
 
 METRIC = "34q 20-cycle circuit time (s), shots/s; fused-TC vs plain FP32 at 1e-5 infid"
+# DRAM bytes (read + write) per amplitude per tensor-core pass, from an ncu capture of the pass
+# on a 2^27-amplitude state (2.087 GB per launch); the traffic of a pass is proportional to the
+# state size, so a launch at n qubits moves this x 2^n.
+TC_DRAM_BYTES_PER_AMP = 2.087e9 / 2**27
 WORKLOAD = "34q_5x7m1_20cyc"
 
 
@@ -276,7 +280,8 @@ def main():
     bytes_per_launch = 16.0 * 2.0**n
     achieved = bytes_per_launch / t_pass_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "frac": achieved / peaks["hbm_gbs"], "traffic": TC_DRAM_BYTES_PER_AMP * 2.0**n,
+                "traffic_src": "ncu capture at 27 qubits scaled by 2^(n-27)",
                 "kernel": "k_fused_tc", "peak_src": peaks["src"],
                 "algorithmic_bytes_per_launch": bytes_per_launch, "launches_per_step": passes}
 

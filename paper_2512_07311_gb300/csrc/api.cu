@@ -168,10 +168,7 @@ int run_passes(rcs_ctx *c, const Plan &plan, const uint8_t *d_ops) {
             case PASS_TC: rc = launch_pass_tc(c->psi, c->n, p, d_ops + plan.tc_offset[i], c->d_err, c->stream); break;
             default: rc = RCS_ERR_ARG;
         }
-        if (rc != RCS_OK) {
-            cudaError_t e = cudaGetLastError();
-            return fail(c, rc, "launch of pass " + std::to_string(i) + " failed: " + cudaGetErrorString(e));
-        }
+        if (rc != RCS_OK) return fail(c, rc, "launch of pass " + std::to_string(i) + " failed: " + take_launch_error());
     }
     c->sums_valid = false;
     return RCS_OK;
@@ -181,7 +178,7 @@ int ensure_sums(rcs_ctx *c) {
     if (c->sums_valid) return RCS_OK;
     int rc = launch_block_sums(c->psi, c->n, c->bsum, c->d_err, c->stream);
     if (rc == RCS_OK) rc = launch_block_scan(c->bsum, c->bpre, c->chunk, c->total, c->n, c->d_err, c->stream);
-    if (rc != RCS_OK) return fail(c, rc, std::string("reduction launch failed: ") + cudaGetErrorString(cudaGetLastError()));
+    if (rc != RCS_OK) return fail(c, rc, "reduction launch failed: " + take_launch_error());
     c->sums_valid = true;
     return RCS_OK;
 }
@@ -189,6 +186,24 @@ int ensure_sums(rcs_ctx *c) {
 }  // namespace
 
 namespace rcs {
+thread_local std::string g_launch_err;
+
+int note_launch_error(const char *what, cudaError_t e) {
+    g_launch_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return RCS_ERR_CUDA;
+}
+
+int launch_status(const char *what) {
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? RCS_OK : note_launch_error(what, e);
+}
+
+std::string take_launch_error() {
+    std::string s;
+    s.swap(g_launch_err);
+    return s.empty() ? std::string("unknown launch failure") : s;
+}
+
 int set_thread_error(int code, const std::string &msg) {
     g_err = msg;
     return code;
@@ -300,7 +315,7 @@ int rcs_create(const rcs_grid *grid, const rcs_opts *opts, rcs_ctx **out) {
     if ((rc = alloc(reinterpret_cast<void **>(&c->total), 8, "total")) != RCS_OK) return rc;
     if ((rc = alloc(reinterpret_cast<void **>(&c->d_err), sizeof(int), "error word")) != RCS_OK) return rc;
     if (cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess || launch_init_zero(c->psi, c->n, c->stream) != RCS_OK) {
-        std::string msg = std::string("initialisation: ") + cudaGetErrorString(cudaGetLastError());
+        std::string msg = "initialisation: " + take_launch_error();
         rcs_destroy(c);
         return fail(nullptr, RCS_ERR_CUDA, msg);
     }
@@ -320,7 +335,7 @@ int rcs_reset(rcs_ctx *c) {
     if (!c) return fail(nullptr, RCS_ERR_ARG, "null context");
     c->sums_valid = false;
     if (launch_init_zero(c->psi, c->n, c->stream) != RCS_OK)
-        return fail(c, RCS_ERR_CUDA, std::string("reset: ") + cudaGetErrorString(cudaGetLastError()));
+        return fail(c, RCS_ERR_CUDA, "reset: " + take_launch_error());
     return RCS_OK;
 }
 
@@ -523,7 +538,7 @@ int rcs_amplitudes(rcs_ctx *c, const uint64_t *bits, size_t n, double *out_re_im
     if ((rc = ensure_u64(c, n)) != RCS_OK || (rc = ensure_f64(c, 2 * n)) != RCS_OK) return rc;
     RCS_CUDA(c, cudaMemcpyAsync(c->d_u64, bits, n * 8, cudaMemcpyHostToDevice, c->stream), "upload bitstrings");
     if (launch_gather(c->psi, c->n, c->d_u64, n, c->d_f64, c->d_err, c->stream) != RCS_OK)
-        return fail(c, RCS_ERR_CUDA, std::string("gather launch: ") + cudaGetErrorString(cudaGetLastError()));
+        return fail(c, RCS_ERR_CUDA, "gather launch: " + take_launch_error());
     RCS_CUDA(c, cudaMemcpyAsync(out_re_im, c->d_f64, n * 16, cudaMemcpyDeviceToHost, c->stream), "download");
     return drain_errors(c);
 }
@@ -577,7 +592,7 @@ int rcs_sample_device(rcs_ctx *c, uint64_t shots, uint64_t seed, uint64_t *d_out
     int rc = ensure_sums(c);
     if (rc != RCS_OK) return rc;
     if (launch_sample(c->psi, c->n, c->bsum, c->bpre, c->total, shots, seed, d_out_bits, c->stream) != RCS_OK)
-        return fail(c, RCS_ERR_CUDA, std::string("sampler launch: ") + cudaGetErrorString(cudaGetLastError()));
+        return fail(c, RCS_ERR_CUDA, "sampler launch: " + take_launch_error());
     return RCS_OK;
 }
 
@@ -603,7 +618,7 @@ int rcs_xeb_device(rcs_ctx *c, const uint64_t *d_samples, size_t n, double *d_ou
     if (rc != RCS_OK) return rc;
     if ((rc = ensure_f64(c, xeb_partials_count(n) + 2)) != RCS_OK) return rc;
     if (launch_xeb(c->psi, c->n, d_samples, n, c->total, c->d_f64, d_out_xeb, c->stream) != RCS_OK)
-        return fail(c, RCS_ERR_CUDA, std::string("xeb launch: ") + cudaGetErrorString(cudaGetLastError()));
+        return fail(c, RCS_ERR_CUDA, "xeb launch: " + take_launch_error());
     return RCS_OK;
 }
 
@@ -620,7 +635,7 @@ int rcs_xeb(rcs_ctx *c, const uint64_t *samples, size_t n, double *out_xeb) {
     if ((rc = ensure_sums(c)) != RCS_OK) return rc;
     double *d_res = c->d_f64 + xeb_partials_count(n);
     if (launch_xeb(c->psi, c->n, c->d_u64, n, c->total, c->d_f64, d_res, c->stream) != RCS_OK)
-        return fail(c, RCS_ERR_CUDA, std::string("xeb launch: ") + cudaGetErrorString(cudaGetLastError()));
+        return fail(c, RCS_ERR_CUDA, "xeb launch: " + take_launch_error());
     RCS_CUDA(c, cudaMemcpyAsync(out_xeb, d_res, 8, cudaMemcpyDeviceToHost, c->stream), "download xeb");
     return drain_errors(c);
 }

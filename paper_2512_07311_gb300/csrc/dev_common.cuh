@@ -49,4 +49,9 @@ inline unsigned grid_for(uint64_t items, unsigned threads, int sms, int per_sm) 
 
 int device_sm_count();
 
+// Launch bookkeeping: the launchers return RCS_ERR_CUDA on failure and leave the
+// CUDA error text for the caller (consumed with take_launch_error()).
+int note_launch_error(const char *what, cudaError_t e);
+int launch_status(const char *what);  // RCS_OK, or notes cudaGetLastError()
+
 }  // namespace rcs

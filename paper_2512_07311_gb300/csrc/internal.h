@@ -19,6 +19,9 @@ constexpr int kTcK = 6;               // width of the tensor-core fused pass
 // Records msg as the calling thread's last error (rcs_last_error(NULL)); returns code.
 int set_thread_error(int code, const std::string &msg);
 
+// Text of the last failed kernel launch on this thread (cleared by the call).
+std::string take_launch_error();
+
 // ---- gates (gates.cpp)
 struct HostGate {
     int nq;

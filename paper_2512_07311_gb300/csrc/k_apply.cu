@@ -197,10 +197,7 @@ __global__ void k_init_zero(float4 *__restrict__ psi4, uint64_t n4) {
         psi4[i] = make_float4(i == 0 ? 1.f : 0.f, 0.f, 0.f, 0.f);
 }
 
-static int check_launch() {
-    cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? RCS_OK : RCS_ERR_CUDA;
-}
+static int check_launch() { return launch_status("state-update kernel"); }
 
 int launch_init_zero(void *psi, int n, void *stream) {
     auto st = static_cast<cudaStream_t>(stream);

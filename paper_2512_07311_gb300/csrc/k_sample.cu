@@ -71,7 +71,7 @@ int launch_block_sums(const void *psi, int n, uint64_t *bsum, int *d_err, void *
     const unsigned grid = grid_for(nblocks * 32, 256, device_sm_count(), 8);
     k_block_sums<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<const float2 *>(psi), bl, nblocks,
                                                                       bsum, d_err);
-    return cudaGetLastError() == cudaSuccess ? RCS_OK : RCS_ERR_CUDA;
+    return launch_status(__func__);
 }
 
 // ---------------------------------------------------------------- scan
@@ -172,7 +172,7 @@ int launch_block_scan(const uint64_t *bsum, uint64_t *bpre, uint64_t *chunk_tot,
     k_scan_chunks<<<nch, kScanThreads, 0, st>>>(bsum, nb, chunk_tot);
     k_scan_top<<<1, kScanThreads, 0, st>>>(chunk_tot, nch, total, d_err);
     k_scan_apply<<<nch, kScanThreads, 0, st>>>(bsum, nb, chunk_tot, bpre);
-    return cudaGetLastError() == cudaSuccess ? RCS_OK : RCS_ERR_CUDA;
+    return launch_status(__func__);
 }
 
 // ---------------------------------------------------------------- Philox4x64-10
@@ -272,7 +272,7 @@ int launch_sample(const void *psi, int n, const uint64_t *bsum, const uint64_t *
     const unsigned grid = grid_for(shots * 32, 256, device_sm_count(), 8);
     k_sample<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<const float2 *>(psi), bl, nblocks, bsum,
                                                                   bpre, total, shots, seed, d_out);
-    return cudaGetLastError() == cudaSuccess ? RCS_OK : RCS_ERR_CUDA;
+    return launch_status(__func__);
 }
 
 // ---------------------------------------------------------------- gather
@@ -298,7 +298,7 @@ int launch_gather(const void *psi, int n, const uint64_t *d_bits, size_t count, 
     if (count == 0) return RCS_OK;
     k_gather<<<grid_for(count, 256, device_sm_count(), 4), 256, 0, static_cast<cudaStream_t>(stream)>>>(
         static_cast<const float2 *>(psi), 1ull << n, d_bits, count, d_out_re_im, d_err);
-    return cudaGetLastError() == cudaSuccess ? RCS_OK : RCS_ERR_CUDA;
+    return launch_status(__func__);
 }
 
 // ---------------------------------------------------------------- XEB
@@ -363,7 +363,7 @@ int launch_xeb(const void *psi, int n, const uint64_t *d_samples, size_t count, 
     k_xeb_partial<<<unsigned(np), kXebThreads, 0, st>>>(static_cast<const float2 *>(psi), 1ull << n, d_samples, count,
                                                         d_partials);
     k_xeb_final<<<1, kXebThreads, 0, st>>>(d_partials, np, count, n, total, d_out);
-    return cudaGetLastError() == cudaSuccess ? RCS_OK : RCS_ERR_CUDA;
+    return launch_status(__func__);
 }
 
 }  // namespace rcs

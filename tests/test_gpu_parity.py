@@ -132,9 +132,13 @@ def test_fused_widths_vs_oracle(lib, oracle, circ20, k_max):
 
 # ------------------------------------------------------------------ tensor-core pass alone
 
+# targets with one below qubit 5 run the memory-order (staged) kernel variant, the
+# others the slice-order variant; n >= 22 gives every CTA several tiles
 @pytest.mark.parametrize("n,targets", [(13, [0, 1, 2, 3, 4, 5]), (13, [7, 8, 9, 10, 11, 12]),
                                        (14, [0, 3, 6, 9, 12, 13]), (16, [2, 5, 1, 15, 8, 11]),
-                                       (22, [21, 0, 10, 4, 17, 6]), (24, [9, 10, 11, 12, 13, 14])])
+                                       (22, [21, 0, 10, 4, 17, 6]), (24, [9, 10, 11, 12, 13, 14]),
+                                       (24, [1, 2, 3, 4, 5, 6]), (22, [5, 9, 14, 17, 20, 21]),
+                                       (23, [0, 1, 2, 7, 14, 22])])
 def test_tc_pass_vs_oracle(lib, oracle, n, targets):
     rng = np.random.default_rng(n * 100 + targets[0])
     psi0 = (rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)).astype(np.complex64)
