@@ -224,6 +224,64 @@ int rcs_xeb(rcs_ctx *ctx, const uint64_t *samples, size_t n, double *out_xeb);
  * An out-of-range sample makes the result NaN. */
 int rcs_xeb_device(rcs_ctx *ctx, const uint64_t *d_samples, size_t n, double *d_out_xeb);
 
+/* ------------------------------------------------------------------ batched circuits */
+
+/* Many independent circuits (different qubit counts and depths) run together: one
+ * persistent kernel applies every fused pass of every circuit, then each circuit is
+ * sampled and scored; the whole sequence is one captured CUDA graph, replayed by
+ * rcs_batch_launch. This is the many-instance form of Section 3.2 items 1, 3, 4. */
+typedef struct rcs_batch rcs_batch;
+
+/* One circuit of a batch: n_qubits (2..30), its host gate list (validated and
+ * copied at creation), the shots to draw (0..2^26) and the sampling seed. */
+typedef struct {
+    int32_t n_qubits;
+    int32_t reserved;
+    const rcs_gate *gates;
+    size_t n_gates;
+    uint64_t shots;
+    uint64_t seed;
+} rcs_batch_item;
+
+/* Builds a batch: allocates every state and sampler buffer, plans every circuit
+ * (FP32 fused passes; opts->k_max in 2..5 fixes the fusion width, 0 or
+ * opts->autotune = 1 lets timed trials of the batched kernel choose it per qubit
+ * count, cached for the process), uploads the work tables and captures the graph.
+ * opts may be NULL (autotune). Synchronous. */
+int rcs_batch_create(const rcs_batch_item *items, size_t n_items, const rcs_opts *opts, rcs_batch **out);
+
+/* Launches the batch's graph on `stream` (cudaStream_t): reset every state to
+ * |0...0>, apply all circuits, sample, score. Asynchronous. */
+int rcs_batch_launch(rcs_batch *batch, uint64_t stream);
+
+/* Synchronises `stream` and reports device-side errors of the last launch:
+ * RCS_ERR_TIMEOUT if a pass waited past its limit for the passes before it (the
+ * kernel then stops taking work and returns), then clears them. */
+int rcs_batch_wait(rcs_batch *batch, uint64_t stream);
+
+/* Number of circuits; per circuit its qubit count, chosen fusion width and pass count. */
+int rcs_batch_size(const rcs_batch *batch);
+int rcs_batch_info(const rcs_batch *batch, size_t i, int32_t *n_qubits, int32_t *k, int64_t *n_passes);
+
+/* Copies circuit i's samples (shots uint64, HOST) and XEB (HOST double) of the last
+ * completed launch; either pointer may be NULL. Synchronous. */
+int rcs_batch_result(rcs_batch *batch, size_t i, uint64_t *out_bits, double *out_xeb);
+
+/* Copies amplitudes [first, first+count) of circuit i's state to host floats. */
+int rcs_batch_state_read(rcs_batch *batch, size_t i, uint64_t first, uint64_t count, float *out_re_im);
+
+/* Test hook for the bounded waits: work item skip_item (>= 0) never publishes its
+ * completion, so the passes after it wait until wait_limit_s and the launch ends
+ * with RCS_ERR_TIMEOUT; skip_item = -1 restores normal operation (limit ~2 s by
+ * default). Recaptures the graph. */
+int rcs_batch_set_fault(rcs_batch *batch, int64_t skip_item, double wait_limit_s);
+
+/* Last error message of the batch. */
+const char *rcs_batch_last_error(const rcs_batch *batch);
+
+/* Frees the batch (synchronises the device first). NULL is a no-op. */
+void rcs_batch_destroy(rcs_batch *batch);
+
 /* ------------------------------------------------------------------ allocation-free scoring */
 
 /* Linear XEB, as rcs_xeb_device, for callers that cannot allocate device memory:

@@ -45,6 +45,11 @@ class rcs_plan_stats(ctypes.Structure):
                 ("hbm_bytes", ctypes.c_double), ("flops", ctypes.c_double)]
 
 
+class rcs_batch_item(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int32), ("reserved", ctypes.c_int32), ("gates", ctypes.c_void_p),
+                ("n_gates", ctypes.c_size_t), ("shots", ctypes.c_uint64), ("seed", ctypes.c_uint64)]
+
+
 _P = ctypes.c_void_p
 _u64p = ctypes.POINTER(ctypes.c_uint64)
 _f64p = ctypes.POINTER(ctypes.c_double)
@@ -77,6 +82,17 @@ SIGNATURES = [
     ("rcs_sample_device", ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p]),
     ("rcs_xeb", ctypes.c_int, [_P, _u64p, ctypes.c_size_t, _f64p]),
     ("rcs_xeb_device", ctypes.c_int, [_P, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("rcs_batch_create", ctypes.c_int, [ctypes.POINTER(rcs_batch_item), ctypes.c_size_t, ctypes.POINTER(rcs_opts),
+                                        ctypes.POINTER(_P)]),
+    ("rcs_batch_launch", ctypes.c_int, [_P, ctypes.c_uint64]),
+    ("rcs_batch_wait", ctypes.c_int, [_P, ctypes.c_uint64]),
+    ("rcs_batch_size", ctypes.c_int, [_P]),
+    ("rcs_batch_info", ctypes.c_int, [_P, ctypes.c_size_t, _i32p, _i32p, ctypes.POINTER(ctypes.c_int64)]),
+    ("rcs_batch_result", ctypes.c_int, [_P, ctypes.c_size_t, _u64p, _f64p]),
+    ("rcs_batch_state_read", ctypes.c_int, [_P, ctypes.c_size_t, ctypes.c_uint64, ctypes.c_uint64, _f32p]),
+    ("rcs_batch_set_fault", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double]),
+    ("rcs_batch_last_error", ctypes.c_char_p, [_P]),
+    ("rcs_batch_destroy", None, [_P]),
     ("rcs_xeb_static", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
                                       ctypes.c_void_p, ctypes.c_uint64]),
 ]
@@ -276,3 +292,64 @@ def rcs_xeb_device(ctx, d_samples: int, n: int, d_out: int):
 def rcs_xeb_static(d_state: int, n_qubits: int, d_samples: int, count: int, d_out: int, stream: int = 0):
     """Allocation-free XEB on caller-owned device buffers (see include/rcs.h)."""
     _check(load().rcs_xeb_static(d_state, n_qubits, d_samples, count, d_out, stream))
+
+
+# ------------------------------------------------------------------ batched circuits
+
+def rcs_batch_create(items, k_max: int = 0, autotune: int = 1):
+    """items: iterable of (n_qubits, gates GATE_DTYPE array, shots, seed)."""
+    items = list(items)
+    arr = (rcs_batch_item * len(items))()
+    keep = []
+    for slot, (n, gates, shots, seed) in zip(arr, items):
+        ptr, k = _gates_ptr(gates, None)
+        keep.append(k)
+        slot.n_qubits = n
+        slot.gates = ptr
+        slot.n_gates = len(k[0])
+        slot.shots = shots
+        slot.seed = seed
+    o = _opts(RCS_PREC_FP32_FUSED, k_max, 0, autotune)
+    out = _P()
+    _check(load().rcs_batch_create(arr, len(items), ctypes.byref(o), ctypes.byref(out)))
+    return out
+
+
+def rcs_batch_launch(batch, stream: int = 0):
+    _check(load().rcs_batch_launch(batch, stream))
+
+
+def rcs_batch_wait(batch, stream: int = 0):
+    _check(load().rcs_batch_wait(batch, stream))
+
+
+def rcs_batch_size(batch) -> int:
+    return load().rcs_batch_size(batch)
+
+
+def rcs_batch_info(batch, i: int) -> dict:
+    n, k, p = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(load().rcs_batch_info(batch, i, ctypes.byref(n), ctypes.byref(k), ctypes.byref(p)))
+    return {"n_qubits": n.value, "k": k.value, "n_passes": p.value}
+
+
+def rcs_batch_result(batch, i: int, shots: int):
+    bits = np.zeros(shots, dtype=np.uint64)
+    xeb = ctypes.c_double()
+    _check(load().rcs_batch_result(batch, i, bits.ctypes.data_as(_u64p) if shots else None, ctypes.byref(xeb)))
+    return bits, xeb.value
+
+
+def rcs_batch_state_read(batch, i: int) -> np.ndarray:
+    n = rcs_batch_info(batch, i)["n_qubits"]
+    out = np.zeros(2 << n, dtype=np.float32)
+    _check(load().rcs_batch_state_read(batch, i, 0, 1 << n, out.ctypes.data_as(_f32p)))
+    return out.view(np.complex64)
+
+
+def rcs_batch_set_fault(batch, skip_item: int, wait_limit_s: float = 2.0):
+    _check(load().rcs_batch_set_fault(batch, skip_item, wait_limit_s))
+
+
+def rcs_batch_destroy(batch):
+    load().rcs_batch_destroy(batch)

@@ -1,0 +1,141 @@
+"""Batched mode (one persistent launch in one captured graph) vs the CPU oracle.
+
+Same tolerances as the single-circuit tests: infidelity <= 1e-5, max amplitude
+error <= 1e-6, sampler agreement with the oracle sampler on the same state
+>= 99.99%, XEB equal to the oracle's on the same samples to 1e-9."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2512_07311_gb300 import build as B
+from paper_2512_07311_gb300 import capi
+from paper_2512_07311_gb300 import circuits as C
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return capi.load()
+
+
+def infidelity(a, b):
+    a = np.asarray(a, dtype=np.complex128)
+    b = np.asarray(b, dtype=np.complex128)
+    return 1.0 - abs(np.vdot(a, b)) ** 2 / (np.vdot(a, a).real * np.vdot(b, b).real)
+
+
+def small_batch():
+    out = []
+    for i, (n, cyc, pat) in enumerate([(12, 6, "ABCDCDAB"), (14, 9, "EFGH"), (16, 12, "ABCDCDAB"),
+                                       (17, 10, "EFGH"), (19, 8, "ABCDCDAB"), (20, 11, "EFGH")]):
+        out.append(C.generate(C.grid_for_n(n), cyc, pat, seed=500 + i, jitter=0.05 * (i % 2)))
+    return out
+
+
+@pytest.mark.parametrize("k_max", [0, 3, 5])
+def test_batch_vs_oracle(lib, oracle, k_max):
+    circs = small_batch()
+    shots = 20_000
+    b = capi.rcs_batch_create([(c.n_qubits, c.gates, shots, 40 + i) for i, c in enumerate(circs)], k_max=k_max,
+                              autotune=int(k_max == 0))
+    try:
+        capi.rcs_batch_launch(b)
+        capi.rcs_batch_wait(b)
+        assert capi.rcs_batch_size(b) == len(circs)
+        for i, c in enumerate(circs):
+            info = capi.rcs_batch_info(b, i)
+            assert info["n_qubits"] == c.n_qubits and 2 <= info["k"] <= 5
+            if k_max:
+                assert info["k"] == min(k_max, c.n_qubits)
+            want = oracle.simulate(c.n_qubits, c.gates)
+            got = capi.rcs_batch_state_read(b, i)
+            assert infidelity(got, want) <= 1e-5
+            assert np.abs(got - want).max() <= 1e-6
+            xs, F = capi.rcs_batch_result(b, i, shots)
+            g128 = got.astype(np.complex128)
+            xo = oracle.sample(g128, shots, 40 + i)
+            assert np.mean(xs == xo) >= 0.9999
+            assert abs(F - oracle.xeb(g128, xs)) <= 1e-9
+    finally:
+        capi.rcs_batch_destroy(b)
+
+
+def test_batch_replay_is_deterministic(lib):
+    circs = small_batch()[:4]
+    b = capi.rcs_batch_create([(c.n_qubits, c.gates, 5000, 7) for c in circs], k_max=4, autotune=0)
+    try:
+        runs = []
+        for _ in range(2):
+            capi.rcs_batch_launch(b)
+            capi.rcs_batch_wait(b)
+            runs.append([capi.rcs_batch_result(b, i, 5000) for i in range(len(circs))])
+        for (x0, f0), (x1, f1) in zip(*runs):
+            np.testing.assert_array_equal(x0, x1)
+            assert f0 == f1
+    finally:
+        capi.rcs_batch_destroy(b)
+
+
+def test_batch_wait_limit_reports_timeout(lib, oracle):
+    """A work item that never publishes its completion makes the next pass of its
+    circuit wait past the limit: the launch ends with RCS_ERR_TIMEOUT, the device
+    stays usable, and a normal launch afterwards gives correct states."""
+    circs = small_batch()[:3]
+    b = capi.rcs_batch_create([(c.n_qubits, c.gates, 1000, 3) for c in circs], k_max=4, autotune=0)
+    try:
+        capi.rcs_batch_set_fault(b, 0, 0.1)  # item 0 = first item of the first pass
+        capi.rcs_batch_launch(b)
+        with pytest.raises(capi.RcsError) as e:
+            capi.rcs_batch_wait(b)
+        assert e.value.code == capi.RCS_ERR_TIMEOUT
+        capi.rcs_batch_set_fault(b, -1)
+        capi.rcs_batch_launch(b)
+        capi.rcs_batch_wait(b)
+        for i, c in enumerate(circs):
+            got = capi.rcs_batch_state_read(b, i)
+            assert infidelity(got, oracle.simulate(c.n_qubits, c.gates)) <= 1e-5
+    finally:
+        capi.rcs_batch_destroy(b)
+
+
+def test_batch_rejects_bad_input(lib):
+    c = small_batch()[0]
+    with pytest.raises(capi.RcsError):
+        capi.rcs_batch_create([(c.n_qubits, c.gates, 10, 1), (40, c.gates, 10, 1)])
+    bad = c.gates.copy()
+    bad["q0"][3] = 99
+    with pytest.raises(capi.RcsError) as e:
+        capi.rcs_batch_create([(c.n_qubits, bad, 10, 1)])
+    assert e.value.code == capi.RCS_ERR_QUBIT
+
+
+def test_batched_workload_64(lib, oracle):
+    """The batched workload: 64 circuits, 16-26 qubits, 10-20 cycles, 10^5 shots each."""
+    circs = C.batch_workload(64, 1000)
+    shots = 100_000
+    b = capi.rcs_batch_create([(c.n_qubits, c.gates, shots, c.seed) for c in circs])
+    try:
+        capi.rcs_batch_launch(b)
+        capi.rcs_batch_wait(b)
+        checked = 0
+        for i, c in enumerate(circs):
+            got = capi.rcs_batch_state_read(b, i).astype(np.complex128)
+            p = np.abs(got) ** 2
+            T = p.sum()
+            assert abs(T - 1) <= 1e-5
+            xs, F = capi.rcs_batch_result(b, i, shots)
+            assert (p[xs.astype(np.int64)] > 0).all()
+            # ideal sampling: E[F] = 2^n sum (p/T)^2 - 1, sd = 2^n sd(p(x)/T) / sqrt(N)
+            q = p / T
+            mean = (1 << c.n_qubits) * float(np.sum(q * q)) - 1
+            sd = (1 << c.n_qubits) * math.sqrt(max(float(np.sum(q ** 3)) - float(np.sum(q * q)) ** 2, 0)) / math.sqrt(shots)
+            assert abs(F - mean) <= 6 * sd + 1e-9, (i, F, mean, sd)
+            if c.n_qubits <= 20 and checked < 6:
+                assert infidelity(got, oracle.simulate(c.n_qubits, c.gates)) <= 1e-5
+                checked += 1
+        assert checked >= 3
+    finally:
+        capi.rcs_batch_destroy(b)
