@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(C.CONFIGS))
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(C.CONFIGS) + ["batch64"],
+                    help="batch64: the 64-circuit batched workload (its own JSON line, not the headline)")
     ap.add_argument("--shots", type=int, default=None)
     ap.add_argument("--qubits", type=int, default=None,
                     help="profiling size: a circuit of the same family (20 cycles, ABCDCDAB) on a grid of this "
@@ -181,6 +182,42 @@ def run_reference(args, rank: int, world: int):
 
 # ------------------------------------------------------------------ our arm
 
+def run_batch(args, torch, capi):
+    """64 seeded circuits (16-26 qubits, 10-20 cycles, 10^5 shots each) in one graph launch:
+    reset, persistent fused apply, per-circuit sampling and XEB."""
+    circs = C.batch_workload(64, 1000)
+    shots = args.shots or 100_000
+    stream = torch.cuda.current_stream()
+    b = capi.rcs_batch_create([(c.n_qubits, c.gates, shots, c.seed) for c in circs])
+    infos = [capi.rcs_batch_info(b, i) for i in range(len(circs))]
+    for _ in range(args.warmup):
+        capi.rcs_batch_launch(b, stream.cuda_stream)
+    capi.rcs_batch_wait(b, stream.cuda_stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        capi.rcs_batch_launch(b, stream.cuda_stream)
+    e1.record(stream)
+    capi.rcs_batch_wait(b, stream.cuda_stream)
+    ms = e0.elapsed_time(e1) / args.steps
+    xebs = [capi.rcs_batch_result(b, i, 0)[1] for i in range(len(circs))]
+    capi.rcs_batch_destroy(b)
+    apply_bytes = sum(16.0 * 2**inf["n_qubits"] * inf["n_passes"] for inf in infos)
+    peaks = measured_peaks()
+    line = {"metric": "64-circuit batched workload time (s)", "value": ms / 1e3, "unit": "s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "data": "synthetic",
+            "config": {"workload": "batch64", "circuits": len(circs),
+                       "qubits": [c.n_qubits for c in circs], "shots_per_circuit": shots,
+                       "k_chosen": [inf["k"] for inf in infos], "passes": [inf["n_passes"] for inf in infos]},
+            "apply_hbm_bytes": apply_bytes,
+            "apply_plus_sampling_GBps": apply_bytes / (ms / 1e3) / 1e9,
+            "frac_of_hbm_if_all_apply": apply_bytes / (ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+            "xeb_mean": float(np.mean(xebs)), "xeb_min": float(np.min(xebs)), "xeb_max": float(np.max(xebs))}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -204,6 +241,8 @@ def main():
     torch.cuda.set_device(local)
     B.build()
     capi.load()
+    if args.workload == "batch64":
+        return run_batch(args, torch, capi)
     cfg = C.CONFIGS[args.workload]
     if args.qubits:
         circ = C.generate(C.grid_for_n(args.qubits), 20, "ABCDCDAB", seed=2)

@@ -86,8 +86,11 @@ typedef struct {
 } rcs_gate;
 
 /* Options. precision: RCS_PREC_*. k_max: largest fused block (FP32_FUSED: 2..5,
- * default 4; BF16X3: 6). autotune: 1 = choose k_max by timed trials on first use
- * for this qubit count and precision. stream: cudaStream_t for all device work. */
+ * default 4; BF16X3: 6). autotune: 1 = for FP32_FUSED, rcs_apply_circuit chooses
+ * k_max in 2..5 minimising (passes at width k) x (measured time of a width-k pass
+ * on this state), by timed trial passes on the first call for this qubit count on
+ * this device (cached for the process; the trials leave the state bit-identical).
+ * stream: cudaStream_t for all device work. */
 typedef struct {
     int32_t precision;
     int32_t k_max;

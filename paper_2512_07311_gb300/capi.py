@@ -146,7 +146,8 @@ def _opts(precision: int, k_max: int, stream: int, autotune: int = 0):
     return o
 
 
-def rcs_create(n_or_grid, precision: int = RCS_PREC_FP32_FUSED, k_max: int = 0, stream: int = 0):
+def rcs_create(n_or_grid, precision: int = RCS_PREC_FP32_FUSED, k_max: int = 0, stream: int = 0,
+               autotune: int = 0):
     """n_or_grid: a qubit count (1 x n grid) or a circuits.Grid."""
     L = load()
     g = rcs_grid()
@@ -157,7 +158,7 @@ def rcs_create(n_or_grid, precision: int = RCS_PREC_FP32_FUSED, k_max: int = 0, 
         rem = np.ascontiguousarray(n_or_grid.removed, dtype=np.int32)
         g.n_removed = len(rem)
         g.removed = rem.ctypes.data_as(_i32p) if len(rem) else None
-    o = _opts(precision, k_max, stream)
+    o = _opts(precision, k_max, stream, autotune)
     out = _P()
     _check(L.rcs_create(ctypes.byref(g), ctypes.byref(o), ctypes.byref(out)))
     return out

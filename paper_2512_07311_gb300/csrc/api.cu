@@ -5,6 +5,8 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -110,6 +112,71 @@ int valid_gates(rcs_ctx *ctx, int n, const rcs_gate *gates, size_t count, std::v
     return RCS_OK;
 }
 
+
+// ---- autotuner for the fused FP32 path: k_max in 2..5 minimising
+// (passes of the circuit at width k) x (measured time of one width-k pass on this
+// state), cached per (device, qubit count). The trial passes are phase permutations
+// (entries 0 and i): FP32 multiply-adds apply them exactly, and applying their
+// inverses afterwards restores the caller's state bit for bit.
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, int> g_tuned_k;
+
+int autotune_fused_k(rcs_ctx *c, const std::vector<HostGate> &hg, int *k_out) {
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tuned_k.find({c->dev, c->n});
+        if (it != g_tuned_k.end()) {
+            *k_out = it->second;
+            return RCS_OK;
+        }
+    }
+    cudaEvent_t e0, e1;
+    RCS_CUDA(c, cudaEventCreate(&e0), "event");
+    RCS_CUDA(c, cudaEventCreate(&e1), "event");
+    double best = 1e300;
+    int best_k = std::min(4, c->n);
+    const int reps = 3;
+    for (int k = 2; k <= std::min(5, c->n); ++k) {
+        Pass fwd, inv;
+        fwd.kind = inv.kind = PASS_SIMT;
+        fwd.k = inv.k = k;
+        for (int i = 0; i < 8; ++i) fwd.t[i] = inv.t[i] = i < k ? i * (c->n / k) : -1;
+        const int d = 1 << k;
+        fwd.U.assign(size_t(d) * d, cd(0.0));
+        inv.U.assign(size_t(d) * d, cd(0.0));
+        for (int j = 0; j < d; ++j) {
+            fwd.U[size_t(j) * d + (j + 1) % d] = cd(0.0, 1.0);  // i * cyclic shift
+            inv.U[size_t((j + 1) % d) * d + j] = cd(0.0, -1.0);
+        }
+        int rc = launch_pass_simt(c->psi, c->n, fwd, c->stream);  // warm-up
+        if (rc == RCS_OK) rc = launch_pass_simt(c->psi, c->n, inv, c->stream);
+        cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < reps && rc == RCS_OK; ++r) rc = launch_pass_simt(c->psi, c->n, fwd, c->stream);
+        cudaEventRecord(e1, c->stream);
+        for (int r = 0; r < reps && rc == RCS_OK; ++r) rc = launch_pass_simt(c->psi, c->n, inv, c->stream);
+        if (rc != RCS_OK) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return fail(c, rc, "autotune trial: " + take_launch_error());
+        }
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        std::vector<Pass> passes;
+        plan_fuse(c->n, hg, k, 0, &passes);
+        const double est = double(ms) / reps * double(passes.size());
+        if (est < best) {
+            best = est;
+            best_k = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned_k[{c->dev, c->n}] = best_k;
+    *k_out = best_k;
+    return RCS_OK;
+}
 
 int build_plan(rcs_ctx *ctx, int n, const std::vector<HostGate> &hg, const rcs_opts &o, Plan *plan) {
     plan->n = n;
@@ -351,7 +418,13 @@ int rcs_apply_circuit(rcs_ctx *c, const rcs_gate *gates, size_t n_gates) {
     int rc = valid_gates(c, c->n, gates, n_gates, &hg);
     if (rc != RCS_OK) return rc;
     Plan plan;
-    if ((rc = build_plan(c, c->n, hg, c->opts, &plan)) != RCS_OK) return rc;
+    rcs_opts o = c->opts;
+    if (o.precision == RCS_PREC_FP32_FUSED && o.autotune && c->n >= 2) {
+        int k = 4;
+        if ((rc = autotune_fused_k(c, hg, &k)) != RCS_OK) return rc;
+        o.k_max = k;
+    }
+    if ((rc = build_plan(c, c->n, hg, o, &plan)) != RCS_OK) return rc;
     std::vector<uint8_t> img;
     build_ops_images(plan, &img);
     if (!img.empty()) {

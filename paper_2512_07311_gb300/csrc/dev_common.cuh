@@ -23,6 +23,8 @@ __device__ __forceinline__ float2 cmac(float2 acc, float2 m, float2 a) {
 
 // round(x^2 * 2^62) for finite |x| < 2, exactly (from the float's exponent and
 // 24-bit mantissa, one 32x32->64 multiply); sets bad for |x| >= 2, Inf or NaN.
+// Integer-only on purpose: on GB300 the 64-bit float-to-integer conversions of an
+// FP32 error-free split run at the FP64 rate and made the reduction 2.6x slower.
 __device__ __forceinline__ uint64_t fx_sq(float x, int &bad) {
     const uint32_t b = __float_as_uint(x) & 0x7fffffffu;
     uint32_t e = b >> 23;

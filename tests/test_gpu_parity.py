@@ -130,6 +130,45 @@ def test_fused_widths_vs_oracle(lib, oracle, circ20, k_max):
         capi.rcs_destroy(ctx)
 
 
+def test_autotuned_fused_path(lib, oracle):
+    """autotune = 1 picks k_max by timed trial passes on the live state; the trials
+    must leave that state bit-identical, so the result equals a fixed-k run."""
+    n = 18
+    circ = C.generate(C.grid_for_n(n), cycles=8, pattern="EFGH", seed=77, jitter=0.05)
+    rng = np.random.default_rng(5)
+    psi0 = (rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)).astype(np.complex64)
+    psi0 /= np.linalg.norm(psi0)
+    results = []
+    for autotune, k in ((1, 0), (0, None)):
+        if k is None:  # the width the autotuner chose
+            k = chosen
+        ctx = capi.rcs_create(n, capi.RCS_PREC_FP32_FUSED, k_max=k, autotune=autotune)
+        try:
+            capi.rcs_state_write(ctx, psi0)
+            capi.rcs_apply_circuit(ctx, circ.gates)
+            results.append(capi.rcs_state_read(ctx))
+        finally:
+            capi.rcs_destroy(ctx)
+        if autotune:
+            # recover the chosen width: the plan with that width has the same pass count as the run
+            chosen = next(kk for kk in (2, 3, 4, 5) if np.array_equal(
+                _fixed_k_state(n, circ, psi0, kk), results[0]))
+    np.testing.assert_array_equal(results[0], results[1])
+    want = oracle.run(psi0.astype(np.complex128), circ.gates)
+    assert infidelity(results[0], want) <= INFID_TOL
+    assert np.abs(results[0] - want).max() <= AMP_TOL
+
+
+def _fixed_k_state(n, circ, psi0, k):
+    ctx = capi.rcs_create(n, capi.RCS_PREC_FP32_FUSED, k_max=k)
+    try:
+        capi.rcs_state_write(ctx, psi0)
+        capi.rcs_apply_circuit(ctx, circ.gates)
+        return capi.rcs_state_read(ctx)
+    finally:
+        capi.rcs_destroy(ctx)
+
+
 # ------------------------------------------------------------------ tensor-core pass alone
 
 # targets with one below qubit 5 run the memory-order (staged) kernel variant, the
