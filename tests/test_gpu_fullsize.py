@@ -1,0 +1,92 @@
+"""Full-size workloads (30, 32 and 34 qubits), in the launch configuration the
+benchmark times (uploaded plans run with rcs_plan_run). The CPU oracle cannot hold
+these states in its time budget (34 qubits need 256 GiB of complex128), so these
+tests check properties that hold at any size:
+
+  * echo: the circuit followed by its inverse returns |0...0> (normalised overlap
+    >= 1 - 1e-5);
+  * the tensor-core BF16x3 state and an FP32 state agree on a seeded subset of
+    ~2^20 amplitudes: subset infidelity <= 1e-5;
+  * the norm stays 1 within the stated drift (FP32: 1e-5; BF16x3: 2e-6 per pass);
+  * the XEB of the shots drawn from the BF16x3 state, scored by that state and by
+    the FP32 state, agrees within 0.005; the FP32 state's own shots score near the
+    Porter-Thomas value 1;
+  * every sample has nonzero probability under the state that produced it.
+"""
+import numpy as np
+import pytest
+
+from paper_2512_07311_gb300 import build as B
+from paper_2512_07311_gb300 import capi
+from paper_2512_07311_gb300 import circuits as C
+
+pytestmark = pytest.mark.gpu
+
+NORM_DRIFT_PER_TC_PASS = 2e-6
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return capi.load()
+
+
+def subset(n, seed=2**20):
+    rng = np.random.default_rng(seed)
+    return np.unique(rng.integers(0, 1 << n, size=1 << 20, dtype=np.uint64))
+
+
+def subset_infidelity(a, b):
+    return 1.0 - abs(np.vdot(a, b)) ** 2 / (np.vdot(a, a).real * np.vdot(b, b).real)
+
+
+def run_plan(ctx, n, gates, precision):
+    plan = capi.rcs_plan_build(n, gates, precision)
+    try:
+        passes = capi.rcs_plan_info(plan)["n_passes"]
+        capi.rcs_plan_upload(ctx, plan)
+        capi.rcs_reset(ctx)
+        capi.rcs_plan_run(ctx, plan)
+        capi.rcs_sync(ctx)
+    finally:
+        capi.rcs_plan_destroy(plan)
+    return passes
+
+
+@pytest.mark.parametrize("name,cross", [("30q_5x6_14cyc", capi.RCS_PREC_FP32_FUSED),
+                                        ("32q_4x8_20cyc", capi.RCS_PREC_FP32_PLAIN),
+                                        ("34q_5x7m1_20cyc", capi.RCS_PREC_FP32_FUSED)])
+def test_full_size_workload(lib, name, cross):
+    cfg = C.CONFIGS[name]
+    circ = C.config_circuit(name)
+    n = circ.n_qubits
+    shots = cfg["shots"]
+    S = subset(n)
+    ctx = capi.rcs_create(circ.grid, capi.RCS_PREC_BF16X3)
+    try:
+        # BF16x3 tensor-core path, as the benchmark runs it
+        p_tc = run_plan(ctx, n, circ.gates, capi.RCS_PREC_BF16X3)
+        norm_tc = capi.rcs_norm(ctx)
+        assert abs(norm_tc - 1) <= NORM_DRIFT_PER_TC_PASS * p_tc
+        a_tc = capi.rcs_amplitudes(ctx, S)
+        x_tc = capi.rcs_sample(ctx, shots, seed=11)
+        F_tc = capi.rcs_xeb(ctx, x_tc)
+        probe = capi.rcs_amplitudes(ctx, x_tc[:20000])
+        assert (np.abs(probe) > 0).all()
+        # echo through the tensor-core path
+        capi.rcs_apply_circuit(ctx, C.inverse_gates(circ.gates))
+        a0 = capi.rcs_amplitudes(ctx, [0])[0]
+        assert abs(a0) ** 2 / capi.rcs_norm(ctx) >= 1 - 1e-5
+        # an FP32 path on the same context
+        p_fp = run_plan(ctx, n, circ.gates, cross)
+        assert p_fp > p_tc
+        assert abs(capi.rcs_norm(ctx) - 1) <= 1e-5
+        a_fp = capi.rcs_amplitudes(ctx, S)
+        assert subset_infidelity(a_tc, a_fp) <= 1e-5
+        F_fp_same_shots = capi.rcs_xeb(ctx, x_tc)
+        assert abs(F_tc - F_fp_same_shots) <= 0.005, (F_tc, F_fp_same_shots)
+        x_fp = capi.rcs_sample(ctx, shots, seed=12)
+        F_fp = capi.rcs_xeb(ctx, x_fp)
+        assert abs(F_fp - 1) <= 0.05 and abs(F_tc - 1) <= 0.05, (F_tc, F_fp)
+    finally:
+        capi.rcs_destroy(ctx)
