@@ -142,7 +142,15 @@ int rcs_reset(rcs_ctx *ctx);
  * The gate list is validated (kinds, qubit range, distinct targets, unitarity of
  * U1/U2), fused by the planner of the context's precision into passes, uploaded
  * and launched. The gate array may be freed when the call returns; the launches
- * are asynchronous on the context's stream. */
+ * are asynchronous on the context's stream.
+ *
+ * Qubit layout: on a fresh state (after rcs_create or rcs_reset, which |0...0> makes
+ * layout-free) the fused paths may store the circuit's qubits in a permuted bit
+ * order, chosen so that no fused pass targets two of the five lowest index bits
+ * (such passes cannot stream memory at full rate). This is invisible to the caller:
+ * samples, amplitudes and XEB use the circuit's own qubit numbering, later circuits
+ * follow the layout, and rcs_state_read/write/device first restore the identity
+ * layout (at most five exact swap passes). rcs_qubit_layout reports it. */
 int rcs_apply_circuit(rcs_ctx *ctx, const rcs_gate *gates, size_t n_gates);
 
 /* Applies one dense k-qubit unitary (1 <= k <= 6) to targets[0..k-1] (distinct,
@@ -157,6 +165,11 @@ int rcs_apply_unitary(rcs_ctx *ctx, int k, const int32_t *targets, const double 
  * own copy of everything it needs. */
 int rcs_plan_build(int n_qubits, const rcs_gate *gates, size_t n_gates, const rcs_opts *opts, rcs_plan **out);
 
+/* Layout a plan stores its circuit in: phys_of[q] = index bit of circuit qubit q
+ * (n_qubits entries; the identity unless the planner chose one, see
+ * rcs_apply_circuit). A plan with a non-identity layout runs only on a fresh state. */
+int rcs_plan_layout(const rcs_plan *plan, int32_t *phys_of);
+
 /* Statistics of a plan. */
 int rcs_plan_info(const rcs_plan *plan, rcs_plan_stats *out);
 
@@ -170,7 +183,8 @@ int rcs_plan_pass(const rcs_plan *plan, size_t i, int32_t *k, int32_t *targets, 
  * and context; later calls are no-ops). */
 int rcs_plan_upload(rcs_ctx *ctx, rcs_plan *plan);
 
-/* Launches every pass of an uploaded plan on the current state (asynchronous). */
+/* Launches every pass of an uploaded plan on the current state (asynchronous). A
+ * plan with its own layout needs a fresh state (else RCS_ERR_ARG). */
 int rcs_plan_run(rcs_ctx *ctx, rcs_plan *plan);
 
 /* Frees a plan and its device copies. NULL is a no-op. */
@@ -182,8 +196,12 @@ void rcs_plan_destroy(rcs_plan *plan);
  * promoted exactly to complex128). Synchronous. bits[i] < 2^n or RCS_ERR_ARG. */
 int rcs_amplitudes(rcs_ctx *ctx, const uint64_t *bits, size_t n, double *out_re_im);
 
+/* Current qubit layout of the context: phys_of[q] = index bit where circuit qubit q
+ * is stored (n entries). */
+int rcs_qubit_layout(const rcs_ctx *ctx, int32_t *phys_of);
+
 /* Copies amplitudes [first, first+count) of the state to host floats (interleaved
- * re, im; 2*count floats). Synchronous. */
+ * re, im; 2*count floats), in the circuit's qubit numbering. Synchronous. */
 int rcs_state_read(rcs_ctx *ctx, uint64_t first, uint64_t count, float *out_re_im);
 
 /* Overwrites amplitudes [first, first+count) from host floats. Synchronous. */

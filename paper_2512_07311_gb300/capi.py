@@ -68,6 +68,8 @@ SIGNATURES = [
     ("rcs_apply_unitary", ctypes.c_int, [_P, ctypes.c_int, _i32p, _f64p]),
     ("rcs_plan_build", ctypes.c_int, [ctypes.c_int, _P, ctypes.c_size_t, ctypes.POINTER(rcs_opts), ctypes.POINTER(_P)]),
     ("rcs_plan_info", ctypes.c_int, [_P, ctypes.POINTER(rcs_plan_stats)]),
+    ("rcs_plan_layout", ctypes.c_int, [_P, _i32p]),
+    ("rcs_qubit_layout", ctypes.c_int, [_P, _i32p]),
     ("rcs_plan_pass", ctypes.c_int, [_P, ctypes.c_size_t, _i32p, _i32p, _f64p]),
     ("rcs_plan_upload", ctypes.c_int, [_P, _P]),
     ("rcs_plan_run", ctypes.c_int, [_P, _P]),
@@ -204,6 +206,18 @@ def rcs_plan_info(plan) -> dict:
     s = rcs_plan_stats()
     _check(load().rcs_plan_info(plan, ctypes.byref(s)))
     return {f: getattr(s, f) for f, _ in rcs_plan_stats._fields_ if f != "reserved"}
+
+
+def rcs_plan_layout(plan, n: int) -> np.ndarray:
+    out = np.zeros(n, dtype=np.int32)
+    _check(load().rcs_plan_layout(plan, out.ctypes.data_as(_i32p)))
+    return out
+
+
+def rcs_qubit_layout(ctx) -> np.ndarray:
+    out = np.zeros(rcs_num_qubits(ctx), dtype=np.int32)
+    _check(load().rcs_qubit_layout(ctx, out.ctypes.data_as(_i32p)), ctx)
+    return out
 
 
 def rcs_plan_pass(plan, i: int, with_matrix: bool = True):

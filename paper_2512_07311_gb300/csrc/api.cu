@@ -32,6 +32,11 @@ struct rcs_ctx {
     size_t f64_cap = 0;
     uint8_t *d_ops = nullptr;  // tensor-core operand images of rcs_apply_circuit plans
     size_t ops_cap = 0;
+    // Qubit layout: circuit qubit q is stored at index bit phys_of[q]. A fresh state
+    // (|0...0>, after create or reset) looks the same in every layout, so the first
+    // circuit on it may choose one; later circuits follow it.
+    int phys_of[64] = {};
+    bool fresh = true;
     std::string err;
 };
 
@@ -178,10 +183,28 @@ int autotune_fused_k(rcs_ctx *c, const std::vector<HostGate> &hg, int *k_out) {
     return RCS_OK;
 }
 
-int build_plan(rcs_ctx *ctx, int n, const std::vector<HostGate> &hg, const rcs_opts &o, Plan *plan) {
+// Fused plans built with allow_layout may store the circuit in a permuted qubit
+// layout (choose_layout) when that keeps two of the lowest bits out of every pass;
+// plan->phys_of then records it.
+int build_plan(rcs_ctx *ctx, int n, const std::vector<HostGate> &hg, const rcs_opts &o, Plan *plan,
+               bool allow_layout) {
     plan->n = n;
     plan->precision = o.precision;
     plan->n_gates = int64_t(hg.size());
+    plan->phys_of.clear();
+    auto fused = [&](int k, int pad) {
+        const Blocking bl = plan_blocks(n, hg, k);
+        int phys[64];
+        if (allow_layout && choose_layout(n, hg, bl, phys)) {
+            std::vector<HostGate> moved = hg;
+            for (HostGate &g : moved)
+                for (int a = 0; a < g.nq; ++a) g.q[a] = phys[g.q[a]];
+            make_passes(n, moved, bl, pad, &plan->passes);
+            plan->phys_of.assign(phys, phys + n);
+        } else {
+            make_passes(n, hg, bl, pad, &plan->passes);
+        }
+    };
     switch (o.precision) {
         case RCS_PREC_FP32_PLAIN:
             plan->k_max = 2;
@@ -192,23 +215,80 @@ int build_plan(rcs_ctx *ctx, int n, const std::vector<HostGate> &hg, const rcs_o
             if (k < 2 || k > 5) return fail(ctx, RCS_ERR_ARG, "FP32_FUSED k_max must be 2..5");
             plan->k_max = std::min(k, n);
             if (n == 1) plan_plain(n, hg, &plan->passes);
-            else plan_fuse(n, hg, plan->k_max, 0, &plan->passes);
+            else fused(plan->k_max, 0);
             break;
         }
         case RCS_PREC_BF16X3:
             if (o.k_max > 0 && o.k_max != kTcK) return fail(ctx, RCS_ERR_ARG, "BF16X3 uses k_max = 6");
             if (n >= kTcK + 7) {
                 plan->k_max = kTcK;
-                plan_fuse(n, hg, kTcK, kTcK, &plan->passes);
+                fused(kTcK, kTcK);
             } else {  // fewer than one 128-slice tile: the FP32 fused path serves small states
                 plan->k_max = std::min(5, n);
                 if (n == 1) plan_plain(n, hg, &plan->passes);
-                else plan_fuse(n, hg, plan->k_max, 0, &plan->passes);
+                else fused(plan->k_max, 0);
             }
             break;
         default:
             return fail(ctx, RCS_ERR_ARG, "unknown precision");
     }
+    return RCS_OK;
+}
+
+bool layout_identity(const rcs_ctx *c) {
+    for (int q = 0; q < c->n; ++q)
+        if (c->phys_of[q] != q) return false;
+    return true;
+}
+
+void set_identity_layout(rcs_ctx *c) {
+    for (int q = 0; q < 64; ++q) c->phys_of[q] = q;
+}
+
+// caller's basis index -> stored index
+BitMap to_stored(const rcs_ctx *c) {
+    BitMap m = identity_map(c->n);
+    if (layout_identity(c)) return m;
+    m.identity = 0;
+    for (int q = 0; q < c->n; ++q) m.to[q] = uint8_t(c->phys_of[q]);
+    return m;
+}
+
+// stored index -> caller's basis index
+BitMap to_caller(const rcs_ctx *c) {
+    BitMap m = identity_map(c->n);
+    if (layout_identity(c)) return m;
+    m.identity = 0;
+    for (int q = 0; q < c->n; ++q) m.to[c->phys_of[q]] = uint8_t(q);
+    return m;
+}
+
+// Brings the stored state back to the identity layout with exact swap passes
+// (entries 0 and 1, so FP32 moves the amplitudes unchanged).
+int restore_layout(rcs_ctx *c) {
+    int log_of[64];
+    for (int q = 0; q < c->n; ++q) log_of[c->phys_of[q]] = q;
+    for (int p = 0; p < c->n; ++p) {
+        while (log_of[p] != p) {
+            const int l = log_of[p];
+            const int q = c->phys_of[p];  // where circuit qubit p sits now
+            Pass sw;
+            sw.kind = PASS_2Q;
+            sw.k = 2;
+            for (int i = 0; i < 8; ++i) sw.t[i] = -1;
+            sw.t[0] = std::min(p, q);
+            sw.t[1] = std::max(p, q);
+            sw.U.assign(16, cd(0.0));
+            sw.U[0] = sw.U[6] = sw.U[9] = sw.U[15] = 1.0;
+            if (launch_pass_plain(c->psi, c->n, sw, c->stream) != RCS_OK)
+                return fail(c, RCS_ERR_CUDA, "layout swap: " + take_launch_error());
+            c->phys_of[p] = p;
+            c->phys_of[l] = q;
+            log_of[p] = p;
+            log_of[q] = l;
+        }
+    }
+    c->sums_valid = false;
     return RCS_OK;
 }
 
@@ -386,6 +466,8 @@ int rcs_create(const rcs_grid *grid, const rcs_opts *opts, rcs_ctx **out) {
         rcs_destroy(c);
         return fail(nullptr, RCS_ERR_CUDA, msg);
     }
+    set_identity_layout(c);
+    c->fresh = true;
     *out = c;
     return RCS_OK;
     RCS_CATCH(nullptr)
@@ -403,6 +485,8 @@ int rcs_reset(rcs_ctx *c) {
     c->sums_valid = false;
     if (launch_init_zero(c->psi, c->n, c->stream) != RCS_OK)
         return fail(c, RCS_ERR_CUDA, "reset: " + take_launch_error());
+    set_identity_layout(c);  // |0...0> is the same in every layout
+    c->fresh = true;
     return RCS_OK;
 }
 
@@ -424,7 +508,12 @@ int rcs_apply_circuit(rcs_ctx *c, const rcs_gate *gates, size_t n_gates) {
         if ((rc = autotune_fused_k(c, hg, &k)) != RCS_OK) return rc;
         o.k_max = k;
     }
-    if ((rc = build_plan(c, c->n, hg, o, &plan)) != RCS_OK) return rc;
+    // a fresh state may take a new layout; otherwise the circuit follows the current one
+    const bool fresh = c->fresh;
+    if (!fresh && !layout_identity(c))
+        for (HostGate &g : hg)
+            for (int a = 0; a < g.nq; ++a) g.q[a] = c->phys_of[g.q[a]];
+    if ((rc = build_plan(c, c->n, hg, o, &plan, fresh)) != RCS_OK) return rc;
     std::vector<uint8_t> img;
     build_ops_images(plan, &img);
     if (!img.empty()) {
@@ -440,6 +529,11 @@ int rcs_apply_circuit(rcs_ctx *c, const rcs_gate *gates, size_t n_gates) {
         RCS_CUDA(c, cudaMemcpyAsync(c->d_ops, img.data(), img.size(), cudaMemcpyHostToDevice, c->stream),
                  "upload operand images");
     }
+    if (fresh) {
+        set_identity_layout(c);
+        for (size_t q = 0; q < plan.phys_of.size(); ++q) c->phys_of[q] = plan.phys_of[q];
+    }
+    c->fresh = false;
     return run_passes(c, plan, c->d_ops);
     RCS_CATCH(c)
 }
@@ -455,6 +549,10 @@ int rcs_apply_unitary(rcs_ctx *c, int k, const int32_t *targets, const double *u
             return fail(c, RCS_ERR_QUBIT, "bad or repeated target");
         seen |= 1ull << targets[i];
     }
+    if (c->fresh) set_identity_layout(c);
+    int tg[8];
+    for (int i = 0; i < k; ++i) tg[i] = c->phys_of[targets[i]];  // stored positions
+    targets = tg;
     const int d = 1 << k;
     std::vector<cd> U(size_t(d) * d);
     for (size_t e = 0; e < U.size(); ++e) U[e] = cd(u_re_im[2 * e], u_re_im[2 * e + 1]);
@@ -505,6 +603,7 @@ int rcs_apply_unitary(rcs_ctx *c, int k, const int32_t *targets, const double *u
         RCS_CUDA(c, cudaMemcpyAsync(c->d_ops, img.data(), img.size(), cudaMemcpyHostToDevice, c->stream),
                  "upload operand images");
     }
+    c->fresh = false;
     return run_passes(c, plan, c->d_ops);
     RCS_CATCH(c)
 }
@@ -522,7 +621,7 @@ int rcs_plan_build(int n, const rcs_gate *gates, size_t n_gates, const rcs_opts 
     int rc = valid_gates(nullptr, n, gates, n_gates, &hg);
     if (rc != RCS_OK) return rc;
     auto *p = new rcs_plan;
-    rc = build_plan(nullptr, n, hg, o, &p->p);
+    rc = build_plan(nullptr, n, hg, o, &p->p, true);
     if (rc != RCS_OK) {
         delete p;
         return rc;
@@ -591,6 +690,18 @@ int rcs_plan_run(rcs_ctx *c, rcs_plan *plan) {
         int rc = rcs_plan_upload(c, plan);
         if (rc != RCS_OK) return rc;
     }
+    // a plan is built for a fresh state in its own layout
+    if (!plan->p.phys_of.empty()) {
+        if (!c->fresh)
+            return fail(c, RCS_ERR_ARG, "this plan stores the circuit in its own qubit layout and needs a fresh "
+                                        "state (rcs_create or rcs_reset first)");
+        set_identity_layout(c);
+        for (size_t q = 0; q < plan->p.phys_of.size(); ++q) c->phys_of[q] = plan->p.phys_of[q];
+    } else if (!layout_identity(c)) {
+        if (c->fresh) set_identity_layout(c);
+        else if (int rc = restore_layout(c); rc != RCS_OK) return rc;
+    }
+    c->fresh = false;
     return run_passes(c, plan->p, plan->d_ops);
 }
 
@@ -598,6 +709,19 @@ void rcs_plan_destroy(rcs_plan *plan) {
     if (!plan) return;
     if (plan->d_ops) cudaFree(plan->d_ops);
     delete plan;
+}
+
+int rcs_qubit_layout(const rcs_ctx *c, int32_t *phys_of) {
+    if (!c || !phys_of) return fail(nullptr, RCS_ERR_ARG, "null argument");
+    for (int q = 0; q < c->n; ++q) phys_of[q] = c->phys_of[q];
+    return RCS_OK;
+}
+
+int rcs_plan_layout(const rcs_plan *plan, int32_t *phys_of) {
+    if (!plan || !phys_of) return fail(nullptr, RCS_ERR_ARG, "null argument");
+    for (int q = 0; q < plan->p.n; ++q)
+        phys_of[q] = plan->p.phys_of.empty() ? q : plan->p.phys_of[size_t(q)];
+    return RCS_OK;
 }
 
 int rcs_amplitudes(rcs_ctx *c, const uint64_t *bits, size_t n, double *out_re_im) {
@@ -610,7 +734,7 @@ int rcs_amplitudes(rcs_ctx *c, const uint64_t *bits, size_t n, double *out_re_im
     int rc;
     if ((rc = ensure_u64(c, n)) != RCS_OK || (rc = ensure_f64(c, 2 * n)) != RCS_OK) return rc;
     RCS_CUDA(c, cudaMemcpyAsync(c->d_u64, bits, n * 8, cudaMemcpyHostToDevice, c->stream), "upload bitstrings");
-    if (launch_gather(c->psi, c->n, c->d_u64, n, c->d_f64, c->d_err, c->stream) != RCS_OK)
+    if (launch_gather(c->psi, c->n, c->d_u64, n, c->d_f64, c->d_err, to_stored(c), c->stream) != RCS_OK)
         return fail(c, RCS_ERR_CUDA, "gather launch: " + take_launch_error());
     RCS_CUDA(c, cudaMemcpyAsync(out_re_im, c->d_f64, n * 16, cudaMemcpyDeviceToHost, c->stream), "download");
     return drain_errors(c);
@@ -620,6 +744,9 @@ int rcs_state_read(rcs_ctx *c, uint64_t first, uint64_t count, float *out_re_im)
     if (!c) return fail(nullptr, RCS_ERR_ARG, "null context");
     const uint64_t lim = uint64_t(1) << c->n;
     if (first > lim || count > lim - first || (count && !out_re_im)) return fail(c, RCS_ERR_ARG, "bad range");
+    if (!layout_identity(c)) {
+        if (int rc = restore_layout(c); rc != RCS_OK) return rc;
+    }
     if (count)
         RCS_CUDA(c, cudaMemcpyAsync(out_re_im, c->psi + first, count * 8, cudaMemcpyDeviceToHost, c->stream),
                  "read state");
@@ -630,6 +757,10 @@ int rcs_state_write(rcs_ctx *c, uint64_t first, uint64_t count, const float *in_
     if (!c) return fail(nullptr, RCS_ERR_ARG, "null context");
     const uint64_t lim = uint64_t(1) << c->n;
     if (first > lim || count > lim - first || (count && !in_re_im)) return fail(c, RCS_ERR_ARG, "bad range");
+    if (!layout_identity(c)) {
+        if (int rc = restore_layout(c); rc != RCS_OK) return rc;
+    }
+    c->fresh = false;
     if (count)
         RCS_CUDA(c, cudaMemcpyAsync(c->psi + first, in_re_im, count * 8, cudaMemcpyHostToDevice, c->stream),
                  "write state");
@@ -639,7 +770,11 @@ int rcs_state_write(rcs_ctx *c, uint64_t first, uint64_t count, const float *in_
 
 int rcs_state_device(rcs_ctx *c, void **d_state) {
     if (!c || !d_state) return fail(c, RCS_ERR_ARG, "null argument");
+    if (!layout_identity(c)) {
+        if (int rc = restore_layout(c); rc != RCS_OK) return rc;
+    }
     *d_state = c->psi;
+    c->fresh = false;
     c->sums_valid = false;  // the caller may write through the pointer
     return RCS_OK;
 }
@@ -664,7 +799,8 @@ int rcs_sample_device(rcs_ctx *c, uint64_t shots, uint64_t seed, uint64_t *d_out
     if (!d_out_bits) return fail(c, RCS_ERR_ARG, "null output");
     int rc = ensure_sums(c);
     if (rc != RCS_OK) return rc;
-    if (launch_sample(c->psi, c->n, c->bsum, c->bpre, c->total, shots, seed, d_out_bits, c->stream) != RCS_OK)
+    if (launch_sample(c->psi, c->n, c->bsum, c->bpre, c->total, shots, seed, d_out_bits, to_caller(c), c->stream) !=
+        RCS_OK)
         return fail(c, RCS_ERR_CUDA, "sampler launch: " + take_launch_error());
     return RCS_OK;
 }
@@ -690,7 +826,7 @@ int rcs_xeb_device(rcs_ctx *c, const uint64_t *d_samples, size_t n, double *d_ou
     int rc = ensure_sums(c);
     if (rc != RCS_OK) return rc;
     if ((rc = ensure_f64(c, xeb_partials_count(n) + 2)) != RCS_OK) return rc;
-    if (launch_xeb(c->psi, c->n, d_samples, n, c->total, c->d_f64, d_out_xeb, c->stream) != RCS_OK)
+    if (launch_xeb(c->psi, c->n, d_samples, n, c->total, c->d_f64, d_out_xeb, to_stored(c), c->stream) != RCS_OK)
         return fail(c, RCS_ERR_CUDA, "xeb launch: " + take_launch_error());
     return RCS_OK;
 }
@@ -707,7 +843,7 @@ int rcs_xeb(rcs_ctx *c, const uint64_t *samples, size_t n, double *out_xeb) {
     RCS_CUDA(c, cudaMemcpyAsync(c->d_u64, samples, n * 8, cudaMemcpyHostToDevice, c->stream), "upload samples");
     if ((rc = ensure_sums(c)) != RCS_OK) return rc;
     double *d_res = c->d_f64 + xeb_partials_count(n);
-    if (launch_xeb(c->psi, c->n, c->d_u64, n, c->total, c->d_f64, d_res, c->stream) != RCS_OK)
+    if (launch_xeb(c->psi, c->n, c->d_u64, n, c->total, c->d_f64, d_res, to_stored(c), c->stream) != RCS_OK)
         return fail(c, RCS_ERR_CUDA, "xeb launch: " + take_launch_error());
     RCS_CUDA(c, cudaMemcpyAsync(out_xeb, d_res, 8, cudaMemcpyDeviceToHost, c->stream), "download xeb");
     return drain_errors(c);

@@ -471,8 +471,10 @@ int record(rcs_batch *b) {
         if (h.shots == 0) continue;
         if ((rc = launch_block_sums(h.psi, h.n, h.bsum, b->d_err, st)) != RCS_OK ||
             (rc = launch_block_scan(h.bsum, h.bpre, h.chunk, h.total, h.n, b->d_err, st)) != RCS_OK ||
-            (rc = launch_sample(h.psi, h.n, h.bsum, h.bpre, h.total, h.shots, h.seed, h.d_bits, st)) != RCS_OK ||
-            (rc = launch_xeb(h.psi, h.n, h.d_bits, h.shots, h.total, h.d_xeb + 1, h.d_xeb, st)) != RCS_OK)
+            (rc = launch_sample(h.psi, h.n, h.bsum, h.bpre, h.total, h.shots, h.seed, h.d_bits, identity_map(h.n),
+                                st)) != RCS_OK ||
+            (rc = launch_xeb(h.psi, h.n, h.d_bits, h.shots, h.total, h.d_xeb + 1, h.d_xeb, identity_map(h.n), st)) !=
+                RCS_OK)
             return bfail(b, rc, "sampling launch: " + take_launch_error());
     }
     for (size_t j = 0; j < b->side.size(); ++j) {

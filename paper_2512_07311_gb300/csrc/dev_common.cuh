@@ -40,6 +40,15 @@ __device__ __forceinline__ uint64_t fx_sq(float x, int &bad) {
     return ((m2 >> (r - 1)) + 1ull) >> 1;  // round half up
 }
 
+// Applies a bit permutation of basis indices (see BitMap).
+template <class Map>
+__device__ __forceinline__ uint64_t map_bits(const Map &m, uint64_t x) {
+    if (m.identity) return x;
+    uint64_t y = 0;
+    for (int b = 0; b < m.n; ++b) y |= ((x >> b) & 1ull) << m.to[b];
+    return y;
+}
+
 // Grid size for a grid-stride kernel: enough CTAs to fill every SM `per_sm`
 // times, never more than the work needs.
 inline unsigned grid_for(uint64_t items, unsigned threads, int sms, int per_sm) {

@@ -50,6 +50,7 @@ struct Pass {
 
 struct Plan {
     int n = 0;
+    std::vector<int> phys_of;  // stored position of each circuit qubit; empty = identity
     int precision = RCS_PREC_FP32_FUSED;
     int k_max = 4;
     int64_t n_gates = 0;
@@ -63,6 +64,28 @@ struct Plan {
 // Fuses gates into passes. k_max: largest block; pad_to: 0, or a width every
 // block is padded to with identity qubits (the tensor-core path needs k = 6).
 void plan_fuse(int n, const std::vector<HostGate> &gates, int k_max, int pad_to, std::vector<Pass> *out);
+
+// The same in two steps: the blocking (which gates form each pass; independent of
+// how the qubits are labelled), then the passes for a gate list with those blocks.
+struct Blocking {
+    std::vector<std::vector<int>> gates;  // gate indices of each block, in application order
+};
+Blocking plan_blocks(int n, const std::vector<HostGate> &gates, int k_max);
+void make_passes(int n, const std::vector<HostGate> &gates, const Blocking &b, int pad_to, std::vector<Pass> *out);
+
+// Physical position of every logical qubit for a blocking (phys_of[logical]): up
+// to five qubits that never share a block trade places with qubits on bits 0..4
+// (so no pass targets two of the lowest qubits); at most five transpositions.
+// Identity when n < 12. Returns whether the layout differs from the identity.
+bool choose_layout(int n, const std::vector<HostGate> &gates, const Blocking &b, int *phys_of);
+
+// Bit permutation of basis indices: bit i of the input moves to bit to[i].
+struct BitMap {
+    uint8_t to[64];
+    int32_t n;
+    int32_t identity;
+};
+BitMap identity_map(int n);
 
 // Plain per-gate plan: one PASS_1Q / PASS_2Q per gate (targets canonicalised ascending).
 void plan_plain(int n, const std::vector<HostGate> &gates, std::vector<Pass> *out);
@@ -89,12 +112,14 @@ int launch_block_sums(const void *psi, int n, uint64_t *bsum, int *d_err, void *
 size_t scan_chunks(int n);
 int launch_block_scan(const uint64_t *bsum, uint64_t *bpre, uint64_t *chunk_tot, uint64_t *total, int n, int *d_err,
                       void *stream);
+// out_map takes the drawn (stored) index to the caller's basis index; in_map takes
+// the caller's index to the stored one.
 int launch_sample(const void *psi, int n, const uint64_t *bsum, const uint64_t *bpre, const uint64_t *total,
-                  uint64_t shots, uint64_t seed, uint64_t *d_out, void *stream);
+                  uint64_t shots, uint64_t seed, uint64_t *d_out, const BitMap &out_map, void *stream);
 int launch_gather(const void *psi, int n, const uint64_t *d_bits, size_t count, double *d_out_re_im, int *d_err,
-                  void *stream);
+                  const BitMap &in_map, void *stream);
 int launch_xeb(const void *psi, int n, const uint64_t *d_samples, size_t count, const uint64_t *total,
-               double *d_partials, double *d_out, void *stream);
+               double *d_partials, double *d_out, const BitMap &in_map, void *stream);
 size_t xeb_partials_count(size_t count);
 
 }  // namespace rcs

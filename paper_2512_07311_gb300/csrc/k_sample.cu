@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(256) k_sample(const float2 *__restrict__ psi, 
                                                  const uint64_t *__restrict__ bsum,
                                                  const uint64_t *__restrict__ bpre,
                                                  const uint64_t *__restrict__ total, uint64_t shots, uint64_t seed,
-                                                 uint64_t *__restrict__ out) {
+                                                 uint64_t *__restrict__ out, const BitMap out_map) {
     const int lane = threadIdx.x & 31;
     const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
     const uint64_t T = *total;
@@ -260,25 +260,33 @@ __global__ void __launch_bounds__(256) k_sample(const float2 *__restrict__ psi, 
             }
         }
         idx = __shfl_sync(0xffffffffu, idx, L < 0 ? 0 : L);
-        if (lane == 0) out[s] = idx;
+        if (lane == 0) out[s] = map_bits(out_map, idx);
     }
 }
 
+BitMap identity_map(int n) {
+    BitMap m;
+    for (int i = 0; i < 64; ++i) m.to[i] = uint8_t(i);
+    m.n = n;
+    m.identity = 1;
+    return m;
+}
+
 int launch_sample(const void *psi, int n, const uint64_t *bsum, const uint64_t *bpre, const uint64_t *total,
-                  uint64_t shots, uint64_t seed, uint64_t *d_out, void *stream) {
+                  uint64_t shots, uint64_t seed, uint64_t *d_out, const BitMap &out_map, void *stream) {
     if (shots == 0) return RCS_OK;
     const int bl = block_log2(n);
     const uint64_t nblocks = 1ull << (n - bl);
     const unsigned grid = grid_for(shots * 32, 256, device_sm_count(), 8);
     k_sample<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<const float2 *>(psi), bl, nblocks, bsum,
-                                                                  bpre, total, shots, seed, d_out);
+                                                                  bpre, total, shots, seed, d_out, out_map);
     return launch_status(__func__);
 }
 
 // ---------------------------------------------------------------- gather
 
 __global__ void k_gather(const float2 *__restrict__ psi, uint64_t namps, const uint64_t *__restrict__ bits,
-                         uint64_t count, double *__restrict__ out, int *__restrict__ d_err) {
+                         uint64_t count, double *__restrict__ out, int *__restrict__ d_err, const BitMap in_map) {
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += stride) {
         const uint64_t x = bits[i];
@@ -287,17 +295,17 @@ __global__ void k_gather(const float2 *__restrict__ psi, uint64_t namps, const u
             atomicOr(d_err, 4);
             continue;
         }
-        const float2 a = psi[x];
+        const float2 a = psi[map_bits(in_map, x)];
         out[2 * i] = double(a.x);
         out[2 * i + 1] = double(a.y);
     }
 }
 
 int launch_gather(const void *psi, int n, const uint64_t *d_bits, size_t count, double *d_out_re_im, int *d_err,
-                  void *stream) {
+                  const BitMap &in_map, void *stream) {
     if (count == 0) return RCS_OK;
     k_gather<<<grid_for(count, 256, device_sm_count(), 4), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        static_cast<const float2 *>(psi), 1ull << n, d_bits, count, d_out_re_im, d_err);
+        static_cast<const float2 *>(psi), 1ull << n, d_bits, count, d_out_re_im, d_err, in_map);
     return launch_status(__func__);
 }
 
@@ -324,7 +332,7 @@ __device__ double cta_sum_f64(double v) {
 
 __global__ void __launch_bounds__(kXebThreads) k_xeb_partial(const float2 *__restrict__ psi, uint64_t namps,
                                                               const uint64_t *__restrict__ x, uint64_t count,
-                                                              double *__restrict__ partials) {
+                                                              double *__restrict__ partials, const BitMap in_map) {
     const uint64_t beg = uint64_t(blockIdx.x) * kXebPerCta;
     const uint64_t end = beg + kXebPerCta < count ? beg + kXebPerCta : count;
     double s = 0.0;
@@ -335,7 +343,7 @@ __global__ void __launch_bounds__(kXebThreads) k_xeb_partial(const float2 *__res
             bad = true;
             continue;
         }
-        const float2 a = psi[xi];
+        const float2 a = psi[map_bits(in_map, xi)];
         s += double(a.x) * double(a.x) + double(a.y) * double(a.y);
     }
     const int anybad = __syncthreads_or(bad);
@@ -356,12 +364,12 @@ __global__ void __launch_bounds__(kXebThreads) k_xeb_final(const double *__restr
 }
 
 int launch_xeb(const void *psi, int n, const uint64_t *d_samples, size_t count, const uint64_t *total,
-               double *d_partials, double *d_out, void *stream) {
+               double *d_partials, double *d_out, const BitMap &in_map, void *stream) {
     auto st = static_cast<cudaStream_t>(stream);
     if (count == 0) return RCS_ERR_ARG;
     const size_t np = xeb_partials_count(count);
     k_xeb_partial<<<unsigned(np), kXebThreads, 0, st>>>(static_cast<const float2 *>(psi), 1ull << n, d_samples, count,
-                                                        d_partials);
+                                                        d_partials, in_map);
     k_xeb_final<<<1, kXebThreads, 0, st>>>(d_partials, np, count, n, total, d_out);
     return launch_status(__func__);
 }

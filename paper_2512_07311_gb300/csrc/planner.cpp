@@ -184,8 +184,7 @@ std::vector<Block> blocking(const Dag &d, size_t G, int k_max, int window, bool 
 // built -- the plain frontier rule, and best-seed growth with affinity windows of
 // 0, 1, 2, 3 and 6 next gates -- and the one with the fewest blocks is kept (on the
 // 34-qubit 20-cycle workload at k = 6: 51 blocks for the plain rule, 45 kept).
-void plan_fuse(int n, const std::vector<HostGate> &gates, int k_max, int pad_to, std::vector<Pass> *out) {
-    out->clear();
+Blocking plan_blocks(int n, const std::vector<HostGate> &gates, int k_max) {
     const size_t G = gates.size();
     k_max = std::max(2, std::min(k_max, n));
     Dag d;
@@ -208,14 +207,82 @@ void plan_fuse(int n, const std::vector<HostGate> &gates, int k_max, int pad_to,
         std::vector<Block> b = blocking(d, G, k_max, v.first, v.second);
         if (b.size() < best.size()) best = std::move(b);
     }
-    for (const Block &b : best) {
-        uint64_t Q = b.Q;
-        for (int q = n - 1; q >= 0 && std::popcount(Q) < pad_to; --q) Q |= 1ull << q;  // identity on padding qubits
+    Blocking out;
+    out.gates.reserve(best.size());
+    for (Block &b : best) out.gates.push_back(std::move(b.gates));
+    return out;
+}
+
+// Passes for the blocks, each padded to pad_to qubits with the highest qubits it
+// does not use (identity on them).
+void make_passes(int n, const std::vector<HostGate> &gates, const Blocking &b, int pad_to, std::vector<Pass> *out) {
+    out->clear();
+    out->reserve(b.gates.size());
+    for (const std::vector<int> &blk_gates : b.gates) {
+        uint64_t Q = 0;
         std::vector<const HostGate *> blk;
-        blk.reserve(b.gates.size());
-        for (int gi : b.gates) blk.push_back(&gates[gi]);
+        blk.reserve(blk_gates.size());
+        for (int gi : blk_gates) {
+            blk.push_back(&gates[gi]);
+            for (int a = 0; a < gates[gi].nq; ++a) Q |= 1ull << gates[gi].q[a];
+        }
+        for (int q = n - 1; q >= 0 && std::popcount(Q) < pad_to; --q) Q |= 1ull << q;
         out->push_back(make_pass(pad_to > 0 ? PASS_TC : PASS_SIMT, Q, blk));
     }
+}
+
+void plan_fuse(int n, const std::vector<HostGate> &gates, int k_max, int pad_to, std::vector<Pass> *out) {
+    make_passes(n, gates, plan_blocks(n, gates, k_max), pad_to, out);
+}
+
+// Up to five qubits that share no block are placed on bits 0..4, chosen greedily
+// from the qubits in the fewest blocks (lowest index on ties), by swapping places
+// with the qubits that sat there. The state kernels give a warp 32
+// neighbouring slices, which are side by side in memory only while the lowest
+// bits are not targets; with this layout a pass targets at most one of bits 0..4.
+bool choose_layout(int n, const std::vector<HostGate> &gates, const Blocking &b, int *phys_of) {
+    for (int q = 0; q < n; ++q) phys_of[q] = q;
+    if (n < 12) return false;
+    std::vector<uint64_t> masks;
+    masks.reserve(b.gates.size());
+    std::vector<int> count(n, 0);
+    for (const std::vector<int> &blk : b.gates) {
+        uint64_t m = 0;
+        for (int gi : blk)
+            for (int a = 0; a < gates[gi].nq; ++a) m |= 1ull << gates[gi].q[a];
+        masks.push_back(m);
+        for (int q = 0; q < n; ++q) count[q] += int((m >> q) & 1);
+    }
+    std::vector<int> order(n);
+    for (int q = 0; q < n; ++q) order[q] = q;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return count[x] < count[y]; });
+    uint64_t chosen = 0;
+    int picked = 0;
+    for (int q : order) {
+        if (picked == 5) break;
+        bool clash = false;
+        for (uint64_t m : masks)
+            if (((m >> q) & 1) && (m & chosen)) {
+                clash = true;
+                break;
+            }
+        if (clash) continue;
+        chosen |= 1ull << q;
+        ++picked;
+    }
+    // pair the chosen qubits above bit `picked-1` with the unchosen qubits below it: at most
+    // five transpositions, so restoring the identity layout takes at most five swaps
+    std::vector<int> up, down;
+    for (int q = 0; q < n; ++q) {
+        const bool c = (chosen >> q) & 1;
+        if (c && q >= picked) up.push_back(q);
+        if (!c && q < picked) down.push_back(q);
+    }
+    for (size_t i = 0; i < up.size(); ++i) {
+        phys_of[up[i]] = down[i];
+        phys_of[down[i]] = up[i];
+    }
+    return !up.empty();
 }
 
 void plan_plain(int n, const std::vector<HostGate> &gates, std::vector<Pass> *out) {

@@ -59,7 +59,7 @@ def _plan_passes(plan):
 
 @pytest.mark.parametrize("precision,kmax,n", [(capi.RCS_PREC_FP32_FUSED, 2, 10), (capi.RCS_PREC_FP32_FUSED, 4, 10),
                                               (capi.RCS_PREC_FP32_FUSED, 5, 9), (capi.RCS_PREC_BF16X3, 0, 13),
-                                              (capi.RCS_PREC_FP32_PLAIN, 0, 9)])
+                                              (capi.RCS_PREC_FP32_FUSED, 4, 14), (capi.RCS_PREC_FP32_PLAIN, 0, 9)])
 def test_fused_plan_reproduces_circuit(oracle, lib, precision, kmax, n):
     """Applying the planned passes (FP64 matrices) with the oracle equals applying
     the circuit gate by gate with the oracle."""
@@ -68,6 +68,7 @@ def test_fused_plan_reproduces_circuit(oracle, lib, precision, kmax, n):
     plan = capi.rcs_plan_build(n, circ.gates, precision, kmax)
     try:
         info, passes = _plan_passes(plan)
+        phys = capi.rcs_plan_layout(plan, n)
     finally:
         capi.rcs_plan_destroy(plan)
     want = oracle.simulate(n, circ.gates)
@@ -76,7 +77,13 @@ def test_fused_plan_reproduces_circuit(oracle, lib, precision, kmax, n):
         assert list(targets) == sorted(targets)
         np.testing.assert_allclose(U @ U.conj().T, np.eye(len(U)), atol=1e-12)
         oracle.apply_matrix(psi, targets, U)
-    np.testing.assert_allclose(psi, want, atol=1e-12)
+    # the passes act on the stored layout: circuit qubit q sits at bit phys[q]
+    assert sorted(phys.tolist()) == list(range(n))
+    idx = np.arange(1 << n)
+    stored = np.zeros(1 << n, dtype=np.int64)
+    for q in range(n):
+        stored |= ((idx >> q) & 1) << int(phys[q])
+    np.testing.assert_allclose(psi[stored], want, atol=1e-12)
     assert info["n_gates"] == len(circ.gates)
     if precision == capi.RCS_PREC_FP32_PLAIN:
         assert info["n_passes"] == len(circ.gates)
@@ -115,3 +122,19 @@ def test_plan_pass_targets_and_adjoint(oracle, lib):
     want = oracle.apply_matrix(psi0.copy(), [5, 2], Q.conj().T)
     got = oracle.apply_matrix(psi0.copy(), list(t), U)
     np.testing.assert_allclose(got, want, atol=1e-12)
+
+
+def test_layout_keeps_low_bits_apart():
+    """On the 34-qubit workload the chosen layout puts circuit qubits that never share
+    a pass on bits 0..4: no tensor-core pass targets two of them."""
+    circ = C.config_circuit("34q_5x7m1_20cyc")
+    plan = capi.rcs_plan_build(34, circ.gates, capi.RCS_PREC_BF16X3)
+    try:
+        info, passes = _plan_passes(plan)
+        phys = capi.rcs_plan_layout(plan, 34)
+    finally:
+        capi.rcs_plan_destroy(plan)
+    assert sorted(phys.tolist()) == list(range(34))
+    assert sum(int(p != q) for q, p in enumerate(phys)) <= 10  # at most five transpositions
+    for targets, _ in passes:
+        assert sum(1 for t in targets if t < 5) <= 1, targets
