@@ -109,6 +109,9 @@ typedef struct {
     int32_t reserved;
     double hbm_bytes;     /* algorithmic HBM bytes: 16 * 2^n per pass */
     double flops;         /* algorithmic real flops of all passes (x3 for the split-precision path) */
+    int64_t prefix_passes; /* leading passes a run from |0...0> does on a compact sub-state (0: none) */
+    int32_t prefix_qubits; /* qubits of that sub-state */
+    int32_t reserved2;
 } rcs_plan_stats;
 
 /* ------------------------------------------------------------------ context */
@@ -133,7 +136,11 @@ int rcs_num_qubits(const rcs_ctx *ctx);
 /* Changes the stream used for the context's device work (cudaStream_t). */
 int rcs_set_stream(rcs_ctx *ctx, uint64_t stream);
 
-/* Resets the state to |0...0> (asynchronous on the context's stream). */
+/* Resets the state to |0...0>. Lazy: no kernel runs now. A fused circuit started
+ * from |0...0> runs its leading passes -- those whose targets span at most n - 4
+ * qubits, since every other qubit is still |0> -- on a compact sub-state and writes
+ * the whole state in one expansion pass; any other first use fills the state with
+ * |0...0> first. */
 int rcs_reset(rcs_ctx *ctx);
 
 /* ------------------------------------------------------------------ state construction (Section 3.2 item 1) */
@@ -178,6 +185,12 @@ int rcs_plan_info(const rcs_plan *plan, rcs_plan_stats *out);
  * (row-major complex128, interleaved) as planned in FP64. targets must hold 8 ints,
  * u_re_im 2 * 4^k doubles. */
 int rcs_plan_pass(const rcs_plan *plan, size_t i, int32_t *k, int32_t *targets, double *u_re_im);
+
+/* Device time (ms) of the full-state passes of the last rcs_apply_circuit or
+ * rcs_plan_run on this context (CUDA events around them on the context's stream;
+ * the sub-state prefix and expansion are not included), and how many there were.
+ * Waits for those passes to finish. */
+int rcs_last_pass_timing(rcs_ctx *ctx, float *ms, int64_t *full_passes);
 
 /* Uploads the plan's pass table and matrices to the device of ctx (once per plan
  * and context; later calls are no-ops). */

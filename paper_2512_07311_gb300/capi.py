@@ -42,7 +42,8 @@ class rcs_opts(ctypes.Structure):
 class rcs_plan_stats(ctypes.Structure):
     _fields_ = [("n_qubits", ctypes.c_int32), ("precision", ctypes.c_int32), ("n_gates", ctypes.c_int64),
                 ("n_passes", ctypes.c_int64), ("k_max", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("hbm_bytes", ctypes.c_double), ("flops", ctypes.c_double)]
+                ("hbm_bytes", ctypes.c_double), ("flops", ctypes.c_double), ("prefix_passes", ctypes.c_int64),
+                ("prefix_qubits", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
 
 class rcs_batch_item(ctypes.Structure):
@@ -72,6 +73,7 @@ SIGNATURES = [
     ("rcs_qubit_layout", ctypes.c_int, [_P, _i32p]),
     ("rcs_plan_pass", ctypes.c_int, [_P, ctypes.c_size_t, _i32p, _i32p, _f64p]),
     ("rcs_plan_upload", ctypes.c_int, [_P, _P]),
+    ("rcs_last_pass_timing", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int64)]),
     ("rcs_plan_run", ctypes.c_int, [_P, _P]),
     ("rcs_plan_destroy", None, [_P]),
     ("rcs_amplitudes", ctypes.c_int, [_P, _u64p, ctypes.c_size_t, _f64p]),
@@ -205,7 +207,7 @@ def rcs_plan_build(n: int, gates: np.ndarray, precision: int = RCS_PREC_FP32_FUS
 def rcs_plan_info(plan) -> dict:
     s = rcs_plan_stats()
     _check(load().rcs_plan_info(plan, ctypes.byref(s)))
-    return {f: getattr(s, f) for f, _ in rcs_plan_stats._fields_ if f != "reserved"}
+    return {f: getattr(s, f) for f, _ in rcs_plan_stats._fields_ if not f.startswith("reserved")}
 
 
 def rcs_plan_layout(plan, n: int) -> np.ndarray:
@@ -232,6 +234,13 @@ def rcs_plan_pass(plan, i: int, with_matrix: bool = True):
         d = 1 << kk
         mat = u[: 2 * d * d].view(np.complex128).reshape(d, d).copy()
     return t[:kk].copy(), mat
+
+
+def rcs_last_pass_timing(ctx):
+    """(ms, passes) of the full-state passes of the last run on ctx."""
+    ms, n = ctypes.c_float(), ctypes.c_int64()
+    _check(load().rcs_last_pass_timing(ctx, ctypes.byref(ms), ctypes.byref(n)), ctx)
+    return ms.value, n.value
 
 
 def rcs_plan_upload(ctx, plan):

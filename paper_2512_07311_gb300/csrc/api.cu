@@ -37,6 +37,13 @@ struct rcs_ctx {
     // circuit on it may choose one; later circuits follow it.
     int phys_of[64] = {};
     bool fresh = true;
+    // The state is |0...0> but not written yet (create/reset are lazy): the first
+    // fused run from it writes the whole state itself, anything else fills it first.
+    bool zero_pending = false;
+    float2 *d_sub = nullptr;  // compact sub-state for the first passes of a run from |0...0>
+    size_t sub_cap = 0;
+    cudaEvent_t ev_full[2] = {nullptr, nullptr};  // around the full-state passes of the last run
+    int64_t timed_passes = -1;
     std::string err;
 };
 
@@ -266,6 +273,10 @@ BitMap to_caller(const rcs_ctx *c) {
 // Brings the stored state back to the identity layout with exact swap passes
 // (entries 0 and 1, so FP32 moves the amplitudes unchanged).
 int restore_layout(rcs_ctx *c) {
+    if (c->zero_pending) {  // |0...0> in any layout
+        set_identity_layout(c);
+        return RCS_OK;
+    }
     int log_of[64];
     for (int q = 0; q < c->n; ++q) log_of[c->phys_of[q]] = q;
     for (int p = 0; p < c->n; ++p) {
@@ -304,25 +315,79 @@ void build_ops_images(Plan &plan, std::vector<uint8_t> *img) {
         if (plan.tc_offset[i] >= 0) tc_build_ops(plan.passes[i], img->data() + plan.tc_offset[i]);
 }
 
-int run_passes(rcs_ctx *c, const Plan &plan, const uint8_t *d_ops) {
-    for (size_t i = 0; i < plan.passes.size(); ++i) {
-        const Pass &p = plan.passes[i];
-        int rc;
-        switch (p.kind) {
-            case PASS_1Q:
-            case PASS_2Q: rc = launch_pass_plain(c->psi, c->n, p, c->stream); break;
-            case PASS_SIMT: rc = launch_pass_simt(c->psi, c->n, p, c->stream); break;
-            case PASS_TC: rc = launch_pass_tc(c->psi, c->n, p, d_ops + plan.tc_offset[i], c->d_err, c->stream); break;
-            default: rc = RCS_ERR_ARG;
-        }
-        if (rc != RCS_OK) return fail(c, rc, "launch of pass " + std::to_string(i) + " failed: " + take_launch_error());
+int materialize(rcs_ctx *c) {
+    if (!c->zero_pending) return RCS_OK;
+    if (launch_init_zero(c->psi, c->n, c->stream) != RCS_OK) return fail(c, RCS_ERR_CUDA, "reset: " + take_launch_error());
+    c->zero_pending = false;
+    return RCS_OK;
+}
+
+Pass compact_pass(const Pass &p, uint64_t T) {
+    Pass q = p;
+    for (int i = 0; i < p.k; ++i) q.t[i] = std::popcount(T & ((1ull << p.t[i]) - 1ull));
+    return q;
+}
+
+int launch_one(rcs_ctx *c, float2 *psi, int n, const Pass &p, const uint8_t *ops) {
+    switch (p.kind) {
+        case PASS_1Q:
+        case PASS_2Q: return launch_pass_plain(psi, n, p, c->stream);
+        case PASS_SIMT: return launch_pass_simt(psi, n, p, c->stream);
+        case PASS_TC: return launch_pass_tc(psi, n, p, ops, c->d_err, c->stream);
+        default: return RCS_ERR_ARG;
     }
+}
+
+// Launches the plan's passes. from_zero: the state is |0...0> (it may not be written
+// yet); the leading passes that touch few qubits then run on a compact sub-state
+// that one expansion pass writes out as the whole state.
+int run_passes(rcs_ctx *c, const Plan &plan, const uint8_t *d_ops, bool from_zero) {
+    size_t first = 0;
+    uint64_t T = 0;
+    const int pre = from_zero ? plan_prefix(plan, &T) : 0;
+    if (pre > 0) {
+        const int m = std::popcount(T);
+        const size_t bytes = size_t(8) << m;
+        if (bytes > c->sub_cap) {
+            RCS_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
+            cudaFree(c->d_sub);
+            c->d_sub = nullptr;
+            c->sub_cap = 0;
+            RCS_CUDA(c, cudaMalloc(&c->d_sub, bytes), "cudaMalloc sub-state");
+            c->sub_cap = bytes;
+        }
+        if (launch_init_zero(c->d_sub, m, c->stream) != RCS_OK)
+            return fail(c, RCS_ERR_CUDA, "sub-state reset: " + take_launch_error());
+        for (int i = 0; i < pre; ++i) {
+            const Pass q = compact_pass(plan.passes[i], T);
+            const uint8_t *ops = q.kind == PASS_TC ? d_ops + plan.tc_offset[i] : nullptr;
+            if (launch_one(c, c->d_sub, m, q, ops) != RCS_OK)
+                return fail(c, RCS_ERR_CUDA, "launch of sub-state pass " + std::to_string(i) + " failed: " +
+                                                 take_launch_error());
+        }
+        if (launch_expand(c->psi, c->n, c->d_sub, T, c->stream) != RCS_OK)
+            return fail(c, RCS_ERR_CUDA, "expansion: " + take_launch_error());
+        c->zero_pending = false;
+        first = size_t(pre);
+    } else if (int rc = materialize(c); rc != RCS_OK) {
+        return rc;
+    }
+    cudaEventRecord(c->ev_full[0], c->stream);
+    for (size_t i = first; i < plan.passes.size(); ++i) {
+        const Pass &p = plan.passes[i];
+        const uint8_t *ops = p.kind == PASS_TC ? d_ops + plan.tc_offset[i] : nullptr;
+        if (launch_one(c, c->psi, c->n, p, ops) != RCS_OK)
+            return fail(c, RCS_ERR_CUDA, "launch of pass " + std::to_string(i) + " failed: " + take_launch_error());
+    }
+    cudaEventRecord(c->ev_full[1], c->stream);
+    c->timed_passes = int64_t(plan.passes.size() - first);
     c->sums_valid = false;
     return RCS_OK;
 }
 
 int ensure_sums(rcs_ctx *c) {
     if (c->sums_valid) return RCS_OK;
+    if (int rc = materialize(c); rc != RCS_OK) return rc;
     int rc = launch_block_sums(c->psi, c->n, c->bsum, c->d_err, c->stream);
     if (rc == RCS_OK) rc = launch_block_scan(c->bsum, c->bpre, c->chunk, c->total, c->n, c->d_err, c->stream);
     if (rc != RCS_OK) return fail(c, rc, "reduction launch failed: " + take_launch_error());
@@ -400,6 +465,9 @@ void rcs_destroy(rcs_ctx *c) {
     cudaFree(c->d_u64);
     cudaFree(c->d_f64);
     cudaFree(c->d_ops);
+    cudaFree(c->d_sub);
+    if (c->ev_full[0]) cudaEventDestroy(c->ev_full[0]);
+    if (c->ev_full[1]) cudaEventDestroy(c->ev_full[1]);
     cudaSetDevice(prev);
     delete c;
 }
@@ -461,11 +529,13 @@ int rcs_create(const rcs_grid *grid, const rcs_opts *opts, rcs_ctx **out) {
         return rc;
     if ((rc = alloc(reinterpret_cast<void **>(&c->total), 8, "total")) != RCS_OK) return rc;
     if ((rc = alloc(reinterpret_cast<void **>(&c->d_err), sizeof(int), "error word")) != RCS_OK) return rc;
-    if (cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess || launch_init_zero(c->psi, c->n, c->stream) != RCS_OK) {
-        std::string msg = "initialisation: " + take_launch_error();
+    if (cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess || cudaEventCreate(&c->ev_full[0]) != cudaSuccess ||
+        cudaEventCreate(&c->ev_full[1]) != cudaSuccess) {
+        std::string msg = std::string("initialisation: ") + cudaGetErrorString(cudaGetLastError());
         rcs_destroy(c);
         return fail(nullptr, RCS_ERR_CUDA, msg);
     }
+    c->zero_pending = true;  // |0...0>, written on first use
     set_identity_layout(c);
     c->fresh = true;
     *out = c;
@@ -483,8 +553,7 @@ int rcs_set_stream(rcs_ctx *c, uint64_t stream) {
 int rcs_reset(rcs_ctx *c) {
     if (!c) return fail(nullptr, RCS_ERR_ARG, "null context");
     c->sums_valid = false;
-    if (launch_init_zero(c->psi, c->n, c->stream) != RCS_OK)
-        return fail(c, RCS_ERR_CUDA, "reset: " + take_launch_error());
+    c->zero_pending = true;  // written by the next run from |0...0>, or on first other use
     set_identity_layout(c);  // |0...0> is the same in every layout
     c->fresh = true;
     return RCS_OK;
@@ -505,6 +574,7 @@ int rcs_apply_circuit(rcs_ctx *c, const rcs_gate *gates, size_t n_gates) {
     rcs_opts o = c->opts;
     if (o.precision == RCS_PREC_FP32_FUSED && o.autotune && c->n >= 2) {
         int k = 4;
+        if ((rc = materialize(c)) != RCS_OK) return rc;
         if ((rc = autotune_fused_k(c, hg, &k)) != RCS_OK) return rc;
         o.k_max = k;
     }
@@ -534,7 +604,7 @@ int rcs_apply_circuit(rcs_ctx *c, const rcs_gate *gates, size_t n_gates) {
         for (size_t q = 0; q < plan.phys_of.size(); ++q) c->phys_of[q] = plan.phys_of[q];
     }
     c->fresh = false;
-    return run_passes(c, plan, c->d_ops);
+    return run_passes(c, plan, c->d_ops, fresh);
     RCS_CATCH(c)
 }
 
@@ -550,6 +620,7 @@ int rcs_apply_unitary(rcs_ctx *c, int k, const int32_t *targets, const double *u
         seen |= 1ull << targets[i];
     }
     if (c->fresh) set_identity_layout(c);
+    if (int rc = materialize(c); rc != RCS_OK) return rc;
     int tg[8];
     for (int i = 0; i < k; ++i) tg[i] = c->phys_of[targets[i]];  // stored positions
     targets = tg;
@@ -604,7 +675,7 @@ int rcs_apply_unitary(rcs_ctx *c, int k, const int32_t *targets, const double *u
                  "upload operand images");
     }
     c->fresh = false;
-    return run_passes(c, plan, c->d_ops);
+    return run_passes(c, plan, c->d_ops, false);
     RCS_CATCH(c)
 }
 
@@ -648,6 +719,18 @@ int rcs_plan_info(const rcs_plan *plan, rcs_plan_stats *out) {
     }
     out->k_max = kmax;
     out->hbm_bytes = 16.0 * amps * double(p.passes.size());
+    uint64_t T = 0;
+    out->prefix_passes = plan_prefix(p, &T);
+    out->prefix_qubits = out->prefix_passes ? std::popcount(T) : 0;
+    return RCS_OK;
+}
+
+int rcs_last_pass_timing(rcs_ctx *c, float *ms, int64_t *full_passes) {
+    if (!c || !ms || !full_passes) return fail(c, RCS_ERR_ARG, "null argument");
+    if (c->timed_passes < 0) return fail(c, RCS_ERR_ARG, "no circuit has run on this context");
+    RCS_CUDA(c, cudaEventSynchronize(c->ev_full[1]), "event sync");
+    RCS_CUDA(c, cudaEventElapsedTime(ms, c->ev_full[0], c->ev_full[1]), "event time");
+    *full_passes = c->timed_passes;
     return RCS_OK;
 }
 
@@ -701,8 +784,9 @@ int rcs_plan_run(rcs_ctx *c, rcs_plan *plan) {
         if (c->fresh) set_identity_layout(c);
         else if (int rc = restore_layout(c); rc != RCS_OK) return rc;
     }
+    const bool fresh = c->fresh;
     c->fresh = false;
-    return run_passes(c, plan->p, plan->d_ops);
+    return run_passes(c, plan->p, plan->d_ops, fresh);
 }
 
 void rcs_plan_destroy(rcs_plan *plan) {
@@ -732,6 +816,7 @@ int rcs_amplitudes(rcs_ctx *c, const uint64_t *bits, size_t n, double *out_re_im
     for (size_t i = 0; i < n; ++i)
         if (bits[i] >= lim) return fail(c, RCS_ERR_ARG, "bitstring index >= 2^n");
     int rc;
+    if ((rc = materialize(c)) != RCS_OK) return rc;
     if ((rc = ensure_u64(c, n)) != RCS_OK || (rc = ensure_f64(c, 2 * n)) != RCS_OK) return rc;
     RCS_CUDA(c, cudaMemcpyAsync(c->d_u64, bits, n * 8, cudaMemcpyHostToDevice, c->stream), "upload bitstrings");
     if (launch_gather(c->psi, c->n, c->d_u64, n, c->d_f64, c->d_err, to_stored(c), c->stream) != RCS_OK)
@@ -744,6 +829,7 @@ int rcs_state_read(rcs_ctx *c, uint64_t first, uint64_t count, float *out_re_im)
     if (!c) return fail(nullptr, RCS_ERR_ARG, "null context");
     const uint64_t lim = uint64_t(1) << c->n;
     if (first > lim || count > lim - first || (count && !out_re_im)) return fail(c, RCS_ERR_ARG, "bad range");
+    if (int rc = materialize(c); rc != RCS_OK) return rc;
     if (!layout_identity(c)) {
         if (int rc = restore_layout(c); rc != RCS_OK) return rc;
     }
@@ -757,6 +843,7 @@ int rcs_state_write(rcs_ctx *c, uint64_t first, uint64_t count, const float *in_
     if (!c) return fail(nullptr, RCS_ERR_ARG, "null context");
     const uint64_t lim = uint64_t(1) << c->n;
     if (first > lim || count > lim - first || (count && !in_re_im)) return fail(c, RCS_ERR_ARG, "bad range");
+    if (int rc = materialize(c); rc != RCS_OK) return rc;
     if (!layout_identity(c)) {
         if (int rc = restore_layout(c); rc != RCS_OK) return rc;
     }
@@ -770,6 +857,7 @@ int rcs_state_write(rcs_ctx *c, uint64_t first, uint64_t count, const float *in_
 
 int rcs_state_device(rcs_ctx *c, void **d_state) {
     if (!c || !d_state) return fail(c, RCS_ERR_ARG, "null argument");
+    if (int rc = materialize(c); rc != RCS_OK) return rc;
     if (!layout_identity(c)) {
         if (int rc = restore_layout(c); rc != RCS_OK) return rc;
     }

@@ -99,6 +99,14 @@ constexpr int kErrTimeout = 8;       // a bounded wait inside a kernel ran out
 // ---- kernels (launchers; all asynchronous on `stream`)
 
 int launch_init_zero(void *psi, int n, void *stream);
+int launch_expand(void *psi, int n, const void *sub, uint64_t tmask, void *stream);
+
+// Leading passes of a fused plan that a run from |0...0> can do on a compact
+// sub-state: the longest prefix whose targets span at most n - 4 qubits (each
+// sub-state pass then costs at most 1/16 of a full one), widened with untouched
+// qubits to the size the kernels need. Returns the pass count (0: not worth it)
+// and the qubit mask of the sub-state.
+int plan_prefix(const Plan &plan, uint64_t *tmask);
 int launch_pass_plain(void *psi, int n, const Pass &p, void *stream);
 int launch_pass_simt(void *psi, int n, const Pass &p, void *stream);
 int launch_pass_tc(void *psi, int n, const Pass &p, const void *d_ops, int *d_err, void *stream);

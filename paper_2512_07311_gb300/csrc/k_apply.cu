@@ -199,6 +199,49 @@ __global__ void k_init_zero(float4 *__restrict__ psi4, uint64_t n4) {
 
 static int check_launch() { return launch_status("state-update kernel"); }
 
+// Full state from a compact sub-state: psi[i] = sub[c(i)] when every bit of i outside
+// tmask is 0 (c(i) gathers the bits of i at the positions of tmask, in order), else 0.
+// A circuit started from |0...0> leaves every qubit its first passes do not touch in
+// |0>, so those passes can run on the 2^popcount(tmask) sub-state and this one write
+// pass replaces the reset and them.
+struct ExpandArgs {
+    uint64_t tmask;
+    int m;
+    int pos[64];
+};
+
+__global__ void k_expand(float4 *__restrict__ psi4, uint64_t n4, const float2 *__restrict__ sub,
+                         const __grid_constant__ ExpandArgs a) {
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t f = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; f < n4; f += stride) {
+        float2 v[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const uint64_t idx = 2 * f + e;
+            if (idx & ~a.tmask) {
+                v[e] = make_float2(0.f, 0.f);
+            } else {
+                uint64_t c = 0;
+                for (int j = 0; j < a.m; ++j) c |= ((idx >> a.pos[j]) & 1ull) << j;
+                v[e] = sub[c];
+            }
+        }
+        psi4[f] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    }
+}
+
+int launch_expand(void *psi, int n, const void *sub, uint64_t tmask, void *stream) {
+    ExpandArgs a;
+    a.tmask = tmask;
+    a.m = 0;
+    for (int q = 0; q < 64; ++q)
+        if ((tmask >> q) & 1) a.pos[a.m++] = q;
+    const uint64_t n4 = (1ull << n) / 2;
+    k_expand<<<grid_for(n4, 256, device_sm_count(), 8), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<float4 *>(psi), n4, static_cast<const float2 *>(sub), a);
+    return launch_status("state expansion");
+}
+
 int launch_init_zero(void *psi, int n, void *stream) {
     auto st = static_cast<cudaStream_t>(stream);
     if (n == 0) return RCS_ERR_ARG;

@@ -285,6 +285,27 @@ bool choose_layout(int n, const std::vector<HostGate> &gates, const Blocking &b,
     return !up.empty();
 }
 
+int plan_prefix(const Plan &plan, uint64_t *tmask) {
+    const int n = plan.n;
+    const int max_sub = n - 4;
+    uint64_t T = 0;
+    int p = 0, need = 0;
+    for (const Pass &q : plan.passes) {
+        if (q.kind != PASS_TC && q.kind != PASS_SIMT) break;
+        uint64_t m = 0;
+        for (int i = 0; i < q.k; ++i) m |= 1ull << q.t[i];
+        if (std::popcount(T | m) > max_sub) break;
+        T |= m;
+        need = std::max(need, q.kind == PASS_TC ? kTcK + 7 : q.k);
+        ++p;
+    }
+    if (p < 2) return 0;
+    for (int q = 0; q < n && std::popcount(T) < need; ++q) T |= 1ull << q;  // idle |0> qubits
+    if (std::popcount(T) > max_sub) return 0;
+    *tmask = T;
+    return p;
+}
+
 void plan_plain(int n, const std::vector<HostGate> &gates, std::vector<Pass> *out) {
     (void)n;
     out->clear();

@@ -159,6 +159,57 @@ def test_autotuned_fused_path(lib, oracle):
     assert np.abs(results[0] - want).max() <= AMP_TOL
 
 
+def test_substate_prefix_is_exact(lib):
+    """From a fresh |0...0> the leading passes run on a compact sub-state and one
+    expansion pass writes the whole state. Every slice computes exactly what it
+    computes in the full state, so the result equals the same circuit applied to an
+    explicitly written |0...0> (which is not fresh: no prefix) bit for bit. At 11
+    qubits no layout is chosen, so both runs use the same passes."""
+    n = 11
+    circ = C.generate(C.grid_for_n(n), cycles=8, pattern="EFGH", seed=93, jitter=0.05)
+    plan = capi.rcs_plan_build(n, circ.gates, capi.RCS_PREC_FP32_FUSED, 4)
+    info = capi.rcs_plan_info(plan)
+    capi.rcs_plan_destroy(plan)
+    assert info["prefix_passes"] >= 2
+    zero = np.zeros(1 << n, dtype=np.complex64)
+    zero[0] = 1
+    out = []
+    for fresh in (True, False):
+        ctx = capi.rcs_create(n, capi.RCS_PREC_FP32_FUSED, k_max=4)
+        try:
+            if not fresh:
+                capi.rcs_state_write(ctx, zero)
+            capi.rcs_apply_circuit(ctx, circ.gates)
+            ms, full = capi.rcs_last_pass_timing(ctx)
+            assert full == info["n_passes"] - (info["prefix_passes"] if fresh else 0)
+            out.append(capi.rcs_state_read(ctx))
+        finally:
+            capi.rcs_destroy(ctx)
+    np.testing.assert_array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("precision", [capi.RCS_PREC_FP32_FUSED, capi.RCS_PREC_BF16X3])
+def test_substate_prefix_vs_oracle(lib, oracle, precision):
+    n = 22
+    circ = C.generate(C.grid_for_n(n), cycles=10, pattern="ABCDCDAB", seed=91, jitter=0.05)
+    plan = capi.rcs_plan_build(n, circ.gates, precision)
+    info = capi.rcs_plan_info(plan)
+    assert info["prefix_passes"] >= 2 and info["prefix_qubits"] <= n - 4
+    ctx = capi.rcs_create(n, precision)
+    try:
+        capi.rcs_plan_upload(ctx, plan)
+        capi.rcs_plan_run(ctx, plan)
+        ms, full = capi.rcs_last_pass_timing(ctx)
+        assert full == info["n_passes"] - info["prefix_passes"] and ms > 0
+        got = capi.rcs_state_read(ctx)
+    finally:
+        capi.rcs_destroy(ctx)
+        capi.rcs_plan_destroy(plan)
+    want = oracle.simulate(n, circ.gates)
+    assert infidelity(got, want) <= INFID_TOL
+    assert np.abs(got - want).max() <= AMP_TOL
+
+
 def _fixed_k_state(n, circ, psi0, k):
     ctx = capi.rcs_create(n, capi.RCS_PREC_FP32_FUSED, k_max=k)
     try:
