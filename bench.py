@@ -364,14 +364,16 @@ def main():
 
     compare = {}
     if not args.no_compare:
-        # same circuit through the plain FP32 per-gate path and the fused FP32 path (one run each),
-        # and the subset infidelity of the TC state against each on a seeded 2^20-amplitude subset
+        # same circuit through the plain FP32 per-gate path, the fused FP32 path and the TF32x3
+        # tensor-core path (one run each), and the subset infidelity of each tensor-core state
+        # against the fused FP32 state on a seeded 2^20-amplitude subset
         rng = np.random.default_rng(2**20)
         subset = np.unique(rng.integers(0, 1 << n, size=1 << 20, dtype=np.uint64))
         capi.rcs_reset(ctx)
         capi.rcs_plan_run(ctx, plan)
-        a_tc = capi.rcs_amplitudes(ctx, subset)
-        for name, prec, kmax in (("fp32_plain", capi.RCS_PREC_FP32_PLAIN, 0), ("fp32_fused_k4", capi.RCS_PREC_FP32_FUSED, 4)):
+        amps = {"bf16x3": capi.rcs_amplitudes(ctx, subset)}
+        for name, prec, kmax in (("fp32_plain", capi.RCS_PREC_FP32_PLAIN, 0), ("fp32_fused_k4", capi.RCS_PREC_FP32_FUSED, 4),
+                                 ("tf32x3", capi.RCS_PREC_TF32X3, 0)):
             p2 = capi.rcs_plan_build(n, circ.gates, prec, kmax)
             i2 = capi.rcs_plan_info(p2)
             capi.rcs_plan_upload(ctx, p2)
@@ -383,12 +385,17 @@ def main():
             e1.record(stream)
             capi.rcs_sync(ctx)
             t = e0.elapsed_time(e1) / 1e3
-            a = capi.rcs_amplitudes(ctx, subset)
-            ov = abs(np.vdot(a, a_tc)) ** 2 / (np.vdot(a, a).real * np.vdot(a_tc, a_tc).real)
+            amps[name] = capi.rcs_amplitudes(ctx, subset)
             compare[name] = {"apply_s": t, "passes": int(i2["n_passes"]),
-                             "hbm_frac": 16.0 * 2**n * i2["n_passes"] / t / 1e9 / peaks["hbm_gbs"],
-                             "subset_infidelity_vs_bf16x3": 1.0 - ov}
+                             "hbm_frac": 16.0 * 2**n * i2["n_passes"] / t / 1e9 / peaks["hbm_gbs"]}
             capi.rcs_plan_destroy(p2)
+
+        def subset_infidelity(a, b):
+            return float(1.0 - abs(np.vdot(a, b)) ** 2 / (np.vdot(a, a).real * np.vdot(b, b).real))
+
+        ref = amps["fp32_fused_k4"]
+        compare["subset_infidelity_vs_fp32_fused_k4"] = {k: subset_infidelity(amps[k], ref)
+                                                         for k in ("bf16x3", "tf32x3", "fp32_plain")}
         compare["bf16x3_apply_s"] = statistics.median(apply_ms) / 1e3
         compare["speedup_vs_fp32_plain"] = compare["fp32_plain"]["apply_s"] / compare["bf16x3_apply_s"]
 

@@ -62,6 +62,8 @@ extern "C" {
 #define RCS_PREC_FP32_PLAIN 0 /* one kernel launch per gate, FP32 SIMT (the baseline path) */
 #define RCS_PREC_FP32_FUSED 1 /* gates fused into k-qubit unitaries (k <= k_max <= 5), FP32 SIMT */
 #define RCS_PREC_BF16X3 2     /* fused 6-qubit unitaries on tcgen05 tensor cores, BF16 hi/lo split, 3 products, FP32 accumulate */
+#define RCS_PREC_TF32X3 3     /* the same passes with a TF32 hi/lo split (3 products, FP32 accumulate): about
+                               * 2^-21 relative error per product instead of 2^-17, at half the tensor rate */
 
 typedef struct rcs_ctx rcs_ctx;
 typedef struct rcs_plan rcs_plan;
@@ -86,7 +88,7 @@ typedef struct {
 } rcs_gate;
 
 /* Options. precision: RCS_PREC_*. k_max: largest fused block (FP32_FUSED: 2..5,
- * default 4; BF16X3: 6). autotune: 1 = for FP32_FUSED, rcs_apply_circuit chooses
+ * default 4; BF16X3 and TF32X3: 6). autotune: 1 = for FP32_FUSED, rcs_apply_circuit chooses
  * k_max in 2..5 minimising (passes at width k) x (measured time of a width-k pass
  * on this state), by timed trial passes on the first call for this qubit count on
  * this device (cached for the process; the trials leave the state bit-identical).
@@ -163,7 +165,7 @@ int rcs_apply_circuit(rcs_ctx *ctx, const rcs_gate *gates, size_t n_gates);
 /* Applies one dense k-qubit unitary (1 <= k <= 6) to targets[0..k-1] (distinct,
  * local index j = sum_i bit(targets[i]) 2^i); u_re_im holds 2^k x 2^k complex128
  * entries, row-major, interleaved, unitary to 1e-6. k <= 5 runs the FP32 fused
- * kernel; k = 6 needs the BF16X3 precision and n >= 13 (tensor-core kernel),
+ * kernel; k = 6 needs the BF16X3 or TF32X3 precision and n >= 13 (tensor-core kernel),
  * else RCS_ERR_UNSUPPORTED. Asynchronous. */
 int rcs_apply_unitary(rcs_ctx *ctx, int k, const int32_t *targets, const double *u_re_im);
 

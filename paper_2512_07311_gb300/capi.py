@@ -19,8 +19,9 @@ LIB_PATH = os.path.join(_HERE, "_build", "librcs.so")
 
 RCS_OK = 0
 RCS_ERR_ARG, RCS_ERR_QUBIT, RCS_ERR_OOM, RCS_ERR_CUDA, RCS_ERR_TIMEOUT, RCS_ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
-RCS_PREC_FP32_PLAIN, RCS_PREC_FP32_FUSED, RCS_PREC_BF16X3 = 0, 1, 2
-PRECISIONS = {"fp32_plain": RCS_PREC_FP32_PLAIN, "fp32_fused": RCS_PREC_FP32_FUSED, "bf16x3": RCS_PREC_BF16X3}
+RCS_PREC_FP32_PLAIN, RCS_PREC_FP32_FUSED, RCS_PREC_BF16X3, RCS_PREC_TF32X3 = 0, 1, 2, 3
+PRECISIONS = {"fp32_plain": RCS_PREC_FP32_PLAIN, "fp32_fused": RCS_PREC_FP32_FUSED, "bf16x3": RCS_PREC_BF16X3,
+              "tf32x3": RCS_PREC_TF32X3}
 
 
 class RcsError(RuntimeError):

@@ -226,7 +226,8 @@ int build_plan(rcs_ctx *ctx, int n, const std::vector<HostGate> &hg, const rcs_o
             break;
         }
         case RCS_PREC_BF16X3:
-            if (o.k_max > 0 && o.k_max != kTcK) return fail(ctx, RCS_ERR_ARG, "BF16X3 uses k_max = 6");
+        case RCS_PREC_TF32X3:
+            if (o.k_max > 0 && o.k_max != kTcK) return fail(ctx, RCS_ERR_ARG, "the tensor-core paths use k_max = 6");
             if (n >= kTcK + 7) {
                 plan->k_max = kTcK;
                 fused(kTcK, kTcK);
@@ -303,16 +304,19 @@ int restore_layout(rcs_ctx *c) {
     return RCS_OK;
 }
 
-// Builds the BF16 operand images of every tensor-core pass into one host buffer.
+bool plan_tf32(const Plan &plan) { return plan.precision == RCS_PREC_TF32X3; }
+
+// Builds the split operand images of every tensor-core pass into one host buffer.
 void build_ops_images(Plan &plan, std::vector<uint8_t> *img) {
-    const size_t per = tc_ops_bytes();
+    const bool tf32 = plan_tf32(plan);
+    const size_t per = tc_ops_bytes(tf32);
     plan.tc_offset.assign(plan.passes.size(), -1);
     size_t count = 0;
     for (size_t i = 0; i < plan.passes.size(); ++i)
         if (plan.passes[i].kind == PASS_TC) plan.tc_offset[i] = int64_t(per * count++);
     img->assign(per * count, 0);
     for (size_t i = 0; i < plan.passes.size(); ++i)
-        if (plan.tc_offset[i] >= 0) tc_build_ops(plan.passes[i], img->data() + plan.tc_offset[i]);
+        if (plan.tc_offset[i] >= 0) tc_build_ops(plan.passes[i], img->data() + plan.tc_offset[i], tf32);
 }
 
 int materialize(rcs_ctx *c) {
@@ -328,12 +332,12 @@ Pass compact_pass(const Pass &p, uint64_t T) {
     return q;
 }
 
-int launch_one(rcs_ctx *c, float2 *psi, int n, const Pass &p, const uint8_t *ops) {
+int launch_one(rcs_ctx *c, float2 *psi, int n, const Pass &p, const uint8_t *ops, bool tf32) {
     switch (p.kind) {
         case PASS_1Q:
         case PASS_2Q: return launch_pass_plain(psi, n, p, c->stream);
         case PASS_SIMT: return launch_pass_simt(psi, n, p, c->stream);
-        case PASS_TC: return launch_pass_tc(psi, n, p, ops, c->d_err, c->stream);
+        case PASS_TC: return launch_pass_tc(psi, n, p, ops, c->d_err, c->stream, tf32);
         default: return RCS_ERR_ARG;
     }
 }
@@ -361,7 +365,7 @@ int run_passes(rcs_ctx *c, const Plan &plan, const uint8_t *d_ops, bool from_zer
         for (int i = 0; i < pre; ++i) {
             const Pass q = compact_pass(plan.passes[i], T);
             const uint8_t *ops = q.kind == PASS_TC ? d_ops + plan.tc_offset[i] : nullptr;
-            if (launch_one(c, c->d_sub, m, q, ops) != RCS_OK)
+            if (launch_one(c, c->d_sub, m, q, ops, plan_tf32(plan)) != RCS_OK)
                 return fail(c, RCS_ERR_CUDA, "launch of sub-state pass " + std::to_string(i) + " failed: " +
                                                  take_launch_error());
         }
@@ -376,7 +380,7 @@ int run_passes(rcs_ctx *c, const Plan &plan, const uint8_t *d_ops, bool from_zer
     for (size_t i = first; i < plan.passes.size(); ++i) {
         const Pass &p = plan.passes[i];
         const uint8_t *ops = p.kind == PASS_TC ? d_ops + plan.tc_offset[i] : nullptr;
-        if (launch_one(c, c->psi, c->n, p, ops) != RCS_OK)
+        if (launch_one(c, c->psi, c->n, p, ops, plan_tf32(plan)) != RCS_OK)
             return fail(c, RCS_ERR_CUDA, "launch of pass " + std::to_string(i) + " failed: " + take_launch_error());
     }
     cudaEventRecord(c->ev_full[1], c->stream);
@@ -492,7 +496,7 @@ int rcs_create(const rcs_grid *grid, const rcs_opts *opts, rcs_ctx **out) {
     o.precision = RCS_PREC_FP32_FUSED;
     o.k_max = 4;
     if (opts) o = *opts;
-    if (o.precision < RCS_PREC_FP32_PLAIN || o.precision > RCS_PREC_BF16X3)
+    if (o.precision < RCS_PREC_FP32_PLAIN || o.precision > RCS_PREC_TF32X3)
         return fail(nullptr, RCS_ERR_ARG, "unknown precision");
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -656,9 +660,10 @@ int rcs_apply_unitary(rcs_ctx *c, int k, const int32_t *targets, const double *u
     plan.n = c->n;
     plan.precision = c->opts.precision;
     plan.n_gates = 1;
-    if (k == kTcK && c->opts.precision == RCS_PREC_BF16X3 && c->n >= kTcK + 7) p.kind = PASS_TC;
+    const bool tc_prec = c->opts.precision == RCS_PREC_BF16X3 || c->opts.precision == RCS_PREC_TF32X3;
+    if (k == kTcK && tc_prec && c->n >= kTcK + 7) p.kind = PASS_TC;
     else if (k <= 5) p.kind = PASS_SIMT;
-    else return fail(c, RCS_ERR_UNSUPPORTED, "6-qubit unitaries need the BF16X3 path and n >= 13");
+    else return fail(c, RCS_ERR_UNSUPPORTED, "6-qubit unitaries need a tensor-core precision and n >= 13");
     plan.passes.push_back(p);
     std::vector<uint8_t> img;
     build_ops_images(plan, &img);

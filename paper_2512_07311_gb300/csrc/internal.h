@@ -38,7 +38,7 @@ enum PassKind : int32_t {
     PASS_1Q = 0,    // plain per-gate, one qubit
     PASS_2Q = 1,    // plain per-gate, two qubits
     PASS_SIMT = 2,  // fused k-qubit unitary, FP32 SIMT
-    PASS_TC = 3,    // fused 6-qubit unitary, tcgen05 BF16x3
+    PASS_TC = 3,    // fused 6-qubit unitary, tcgen05 split precision (BF16x3 or TF32x3, per plan)
 };
 
 struct Pass {
@@ -57,7 +57,7 @@ struct Plan {
     std::vector<Pass> passes;
     // device copies, per context device (uploaded lazily)
     int dev = -1;
-    void *d_tc_ops = nullptr;   // BF16 hi/lo operand images of PASS_TC passes
+    void *d_tc_ops = nullptr;   // hi/lo operand images of PASS_TC passes
     std::vector<int64_t> tc_offset;  // byte offset of each pass's image (-1 if none)
 };
 
@@ -109,11 +109,13 @@ int launch_expand(void *psi, int n, const void *sub, uint64_t tmask, void *strea
 int plan_prefix(const Plan &plan, uint64_t *tmask);
 int launch_pass_plain(void *psi, int n, const Pass &p, void *stream);
 int launch_pass_simt(void *psi, int n, const Pass &p, void *stream);
-int launch_pass_tc(void *psi, int n, const Pass &p, const void *d_ops, int *d_err, void *stream);
+// tf32: the TF32x3 kernel (operand image from tc_build_ops(p, img, true)), else BF16x3.
+int launch_pass_tc(void *psi, int n, const Pass &p, const void *d_ops, int *d_err, void *stream, bool tf32);
 
-// Size in bytes of the BF16x3 operand image of one 6-qubit pass, and its builder.
-size_t tc_ops_bytes();
-void tc_build_ops(const Pass &p, void *host_image);
+// Size in bytes of the operand image of one 6-qubit pass (BF16x3: 64 KB, TF32x3:
+// 96 KB), and its builder.
+size_t tc_ops_bytes(bool tf32);
+void tc_build_ops(const Pass &p, void *host_image, bool tf32);
 
 // Sampler / readout (k_sample.cu)
 int launch_block_sums(const void *psi, int n, uint64_t *bsum, int *d_err, void *stream);

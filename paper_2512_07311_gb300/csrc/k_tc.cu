@@ -50,28 +50,39 @@ constexpr int kEpiWarps = 8;
 constexpr int kThreads = (kLoaderWarps + kEpiWarps + 1) * 32;  // 544
 constexpr int kOpBytes = NR * KR * 2;                          // one bf16 operand image: 32 KB
 constexpr int kStageBytes = D * M * 8;                         // one tile of complex64: 64 KB
-// shared memory map (offsets from a 1024-aligned base)
-constexpr int kSmBhi = 0;
+constexpr int kSmBhi = 0;                                      // BF16: B_hi image, then B_lo
 constexpr int kSmBlo = kOpBytes;
-constexpr int kSmStage0 = 2 * kOpBytes;
-constexpr int kSmStage1 = kSmStage0 + kStageBytes;
-constexpr int kSmOff = kSmStage1 + kStageBytes;  // 64 x u64 target offsets
-constexpr int kSmHiOff = kSmOff + D * 8;         // 64 x u64 offsets of the high compact bits (memory-order variant)
-constexpr int kSmCj = kSmHiOff + 64 * 8;         // 64 x u16 compact index of local amplitude j
-constexpr int kSmCs = kSmCj + D * 2;             // 128 x u16 compact index of slice s within the tile
-constexpr int kSmBar = kSmCs + M * 2;            // 12 mbarriers
-constexpr int kSmMisc = kSmBar + 12 * 8;         // tmem slot, abort flag
-constexpr int kSmBytes = kSmMisc + 16;
-constexpr int kSmAlloc = kSmBytes + 1024;        // slack for 1024-byte alignment
+// TF32: per split (hi, lo) one K-major image of the 192 x 64 matrix [-Ui; Ur; Ui]
+// (rows = outputs, K = inputs), in two 128-byte swizzle atom columns of 32 inputs.
+constexpr int kTf32Rows = 3 * D;
+constexpr int kTf32Atom = kTf32Rows * 128;   // 24 KB
+constexpr int kTf32Split = 2 * kTf32Atom;    // 48 KB
+// Shared-memory map (offsets from a 1024-aligned base): the B images, two stages of
+// one tile each, then the small tables.
+template <bool kTf32>
+struct Layout {
+    static constexpr int kBBytes = kTf32 ? 2 * kTf32Split : 2 * kOpBytes;
+    static constexpr int kStage0 = kBBytes;
+    static constexpr int kOff = kStage0 + 2 * kStageBytes;  // 64 x u64 target offsets
+    static constexpr int kHiOff = kOff + D * 8;             // 64 x u64 offsets of the high compact bits
+    static constexpr int kCj = kHiOff + 64 * 8;             // 64 x u16 compact index of local amplitude j
+    static constexpr int kCs = kCj + D * 2;                 // 128 x u16 compact index of slice s within the tile
+    static constexpr int kBar = kCs + M * 2;                // 16 mbarriers
+    static constexpr int kMisc = kBar + 16 * 8;             // tmem slot, abort flag
+    static constexpr int kAlloc = kMisc + 16 + 1024;        // slack for 1024-byte alignment
+    static_assert(kAlloc <= 227 * 1024, "shared memory");
+};
 constexpr uint32_t kTmemCols = 512;
 constexpr long long kWaitCycles = 1ll << 31;     // ~1 s at 2 GHz
 // instruction descriptor: D f32, A bf16, B bf16, both K-major, N = 128, M = 128
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(NR >> 3) << 17) | (uint32_t(M >> 4) << 24);
+// TF32 variant: D f32, A tf32, B tf32, both K-major, N = 128 (Re outputs, then Im), M = 128
+constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(128 >> 3) << 17) | (uint32_t(M >> 4) << 24);
 }  // namespace tc
 
 struct TcArgs {
     float2 *psi;
-    const uint4 *ops;  // B_hi image then B_lo image (shared-memory layout, 64 KB)
+    const uint4 *ops;  // B operand images in their shared-memory layout (BF16: 64 KB, TF32: 96 KB)
     int *err;
     uint32_t tiles;
     int t[tc::K];      // ascending targets
@@ -160,6 +171,16 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16
         : "memory");
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
@@ -188,6 +209,16 @@ __device__ __forceinline__ void mma_bf16_tmemA(uint32_t d_tmem, uint32_t a_tmem,
         : "memory");
 }
 
+__device__ __forceinline__ void mma_tf32_tmemA(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                               uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
@@ -199,6 +230,16 @@ __device__ __forceinline__ uint64_t slice_base(uint64_t s, const int (&t)[tc::K]
 }
 
 __device__ __forceinline__ uint32_t bf162_bits(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t *>(&v); }
+
+// x -> tf32 hi = rna(x) and lo = rna(x - hi), as 32-bit words (tf32 keeps 10 mantissa bits).
+__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
+    uint32_t h, l;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    const float r = x - __uint_as_float(h);
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(r));
+    hi = h;
+    lo = l;
+}
 
 // (re, im) -> bf16x2 hi = rn(v) and lo = rn(v - hi); re in the low half (even K index).
 __device__ __forceinline__ void split_bf16x2(float2 v, uint32_t &hi, uint32_t &lo) {
@@ -214,24 +255,34 @@ __device__ __forceinline__ void split_bf16x2(float2 v, uint32_t &hi, uint32_t &l
 // kStaged = true: for passes with low targets, loads and stores walk the tile in
 // memory order (32 consecutive amplitudes per warp instruction) through the
 // swizzled shared-memory stage, which also carries the outputs back out.
-template <bool kStaged>
+// kTf32 = false: BF16 split of the realified operands (24 MMAs of K = 16 per tile).
+// kTf32 = true: TF32 split of the complex block form (48 MMAs of K = 8 per tile).
+template <bool kStaged, bool kTf32>
 __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_constant__ TcArgs a) {
     using namespace tc;
+    using L = Layout<kTf32>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *off = reinterpret_cast<uint64_t *>(sm + kSmOff);
-    const uint32_t bar0 = smem_u32(sm + kSmBar);
+    uint64_t *off = reinterpret_cast<uint64_t *>(sm + L::kOff);
+    const uint32_t bar0 = smem_u32(sm + L::kBar);
     auto bar_full = [&](int b) { return bar0 + 8u * uint32_t(b); };
     auto bar_done = [&](int b) { return bar0 + 16u + 8u * uint32_t(b); };
     auto bar_free = [&](int b) { return bar0 + 32u + 8u * uint32_t(b); };
     auto bar_loaded = [&](int b) { return bar0 + 48u + 8u * uint32_t(b); };    // stage b holds the tile's inputs
     auto bar_outready = [&](int b) { return bar0 + 64u + 8u * uint32_t(b); };  // stage b holds the tile's outputs
     auto bar_sfree = [&](int b) { return bar0 + 80u + 8u * uint32_t(b); };     // stage b read out by the stores
-    uint64_t *hi_off = reinterpret_cast<uint64_t *>(sm + kSmHiOff);
-    uint16_t *cj = reinterpret_cast<uint16_t *>(sm + kSmCj);
-    uint16_t *cs = reinterpret_cast<uint16_t *>(sm + kSmCs);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + kSmMisc);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + kSmMisc + 4);
+    // TF32: A is filled and consumed in two K halves (inputs 0..31 by loader warps 0-3,
+    // 32..63 by warps 4-7). bar_full(b) then counts the first half's warps and
+    // bar_full1(b) the second's; bar_done_a(b) completes once the MMAs that read the
+    // first half are done, bar_done(b) once all of the tile's MMAs are.
+    auto bar_full1 = [&](int b) { return bar0 + 96u + 8u * uint32_t(b); };
+    auto bar_done_a = [&](int b) { return bar0 + 112u + 8u * uint32_t(b); };
+    auto bar_full_h = [&](int b, int h) { return (kTf32 && h) ? bar_full1(b) : bar_full(b); };
+    uint64_t *hi_off = reinterpret_cast<uint64_t *>(sm + L::kHiOff);
+    uint16_t *cj = reinterpret_cast<uint16_t *>(sm + L::kCj);
+    uint16_t *cs = reinterpret_cast<uint16_t *>(sm + L::kCs);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + L::kMisc);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + L::kMisc + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int t[K];
@@ -241,7 +292,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
     // ---- set-up: operand image, offset table, barriers, tensor memory
     {
         uint4 *dst = reinterpret_cast<uint4 *>(sm);
-        for (int i = threadIdx.x; i < 2 * kOpBytes / 16; i += kThreads) dst[i] = a.ops[i];
+        for (int i = threadIdx.x; i < L::kBBytes / 16; i += kThreads) dst[i] = a.ops[i];
         const uint64_t V = a.vmask;
         auto cpos = [&](int qb) { return __popcll(V & ((1ull << qb) - 1ull)); };  // compact position of qubit qb
         if (threadIdx.x < D) {
@@ -280,18 +331,16 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
             cs[threadIdx.x] = uint16_t(c);
         }
         if (threadIdx.x == 0) {
-            mbar_init(bar_full(0), kLoaderWarps);
-            mbar_init(bar_full(1), kLoaderWarps);
-            mbar_init(bar_done(0), 1);
-            mbar_init(bar_done(1), 1);
-            mbar_init(bar_free(0), kEpiWarps);
-            mbar_init(bar_free(1), kEpiWarps);
-            mbar_init(bar_loaded(0), kLoaderWarps * 32);
-            mbar_init(bar_loaded(1), kLoaderWarps * 32);
-            mbar_init(bar_outready(0), kEpiWarps);
-            mbar_init(bar_outready(1), kEpiWarps);
-            mbar_init(bar_sfree(0), kEpiWarps);
-            mbar_init(bar_sfree(1), kEpiWarps);
+            for (int b = 0; b < 2; ++b) {
+                mbar_init(bar_full(b), kTf32 ? kLoaderWarps / 2 : kLoaderWarps);
+                mbar_init(bar_full1(b), kLoaderWarps / 2);
+                mbar_init(bar_done_a(b), 1);
+                mbar_init(bar_done(b), 1);
+                mbar_init(bar_free(b), kEpiWarps);
+                mbar_init(bar_loaded(b), kLoaderWarps * 32);
+                mbar_init(bar_outready(b), kEpiWarps);
+                mbar_init(bar_sfree(b), kEpiWarps);
+            }
             *abort_flag = 0;
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
@@ -310,8 +359,70 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
     const uint32_t ntile = a.tiles;
     const uint32_t my_tiles = blockIdx.x < ntile ? (ntile - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
+    // Tensor-memory plan. BF16: two buffers of {D: 128 cols, A_hi: 64, A_lo: 64} at
+    // column 256 b. TF32: D double-buffered at column 128 b (Re outputs in its first 64
+    // columns, Im in the last 64) and one A region at 256 holding, per K half h, the
+    // 32 columns each of Re_hi, Re_lo, Im_hi, Im_lo at 256 + 128 h. A K half of tile i
+    // is converted once the MMAs of tile i - 1 that read it are done, so converting
+    // one half overlaps the MMAs on the other.
+    auto dcol_of = [&](int b) { return tmem + uint32_t(b) * (kTf32 ? 128u : 256u); };
+    auto acol_of = [&](int b) { return kTf32 ? tmem + 256u : tmem + uint32_t(b) * 256u + 128u; };
+    // The loader warps of K half h may overwrite their part of A for tile i once the
+    // MMAs that read it for the previous tile in that buffer completed.
+    auto wait_a_free = [&](uint32_t i, int h) {
+        if constexpr (kTf32) {
+            if (i < 1) return true;
+            const uint32_t j = i - 1;
+            return warp_wait(h ? bar_done(int(j & 1)) : bar_done_a(int(j & 1)), (j >> 1) & 1, abort_flag);
+        } else {
+            if (i < 2) return true;
+            const uint32_t j = i - 2;
+            return warp_wait(bar_done(int(j & 1)), (j >> 1) & 1, abort_flag);
+        }
+    };
+    // TMEM column of the A region for K half h (TF32) or the A_hi image (BF16).
+    auto abase_of = [&](int b, int h) { return kTf32 ? acol_of(b) + 128u * uint32_t(h) : acol_of(b); };
+    auto acol_in = [&](int h, int ch) { return kTf32 ? 16 * ch : 32 * h + 16 * ch; };
+    // Splits 16 amplitudes (TMEM columns) of one slice and writes them to A.
+    auto put16 = [&](uint32_t abase, int col, const float2 (&v)[16]) {
+        if constexpr (kTf32) {
+            uint32_t hi[16], lo[16];
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) split_tf32(v[jj].x, hi[jj], lo[jj]);
+            tmem_st16(abase + uint32_t(col), hi);
+            tmem_st16(abase + 32u + uint32_t(col), lo);
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) split_tf32(v[jj].y, hi[jj], lo[jj]);
+            tmem_st16(abase + 64u + uint32_t(col), hi);
+            tmem_st16(abase + 96u + uint32_t(col), lo);
+        } else {
+            uint32_t hi[16], lo[16];
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) split_bf16x2(v[jj], hi[jj], lo[jj]);
+            tmem_st16(abase + uint32_t(col), hi);
+            tmem_st16(abase + 64u + uint32_t(col), lo);
+        }
+    };
+    // Reads 16 output amplitudes (j = j0 .. j0 + 15) of one slice from D.
+    auto get16 = [&](uint32_t dbase, int j0, float2 (&v)[16]) {
+        if constexpr (kTf32) {
+            uint32_t re[16], im[16];
+            tmem_ld16(dbase + uint32_t(j0), re);
+            tmem_ld16(dbase + 64u + uint32_t(j0), im);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) v[jj] = make_float2(__uint_as_float(re[jj]), __uint_as_float(im[jj]));
+        } else {
+            uint32_t x[32];
+            tmem_ld32(dbase + uint32_t(2 * j0), x);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) v[jj] = make_float2(__uint_as_float(x[2 * jj]), __uint_as_float(x[2 * jj + 1]));
+        }
+    };
+
     const uint32_t rmask = (1u << a.r) - 1u;
-    const uint32_t stage0_u32 = smem_u32(sm + kSmStage0);
+    const uint32_t stage0_u32 = smem_u32(sm + L::kStage0);
     if (warp < kLoaderWarps && !kStaged) {
         // ---------------------------------------------------------------- loaders (slice order)
         const int q = warp & 3, h = warp >> 2;  // TMEM lane quarter, amplitude half
@@ -334,25 +445,21 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
             const int b = i & 1;
             if (i + 1 < my_tiles) asm volatile("cp.async.wait_group 1;" ::: "memory");
             else asm volatile("cp.async.wait_group 0;" ::: "memory");
-            if (i >= 2 && !warp_wait(bar_done(b), ((i >> 1) - 1) & 1, abort_flag)) break;
+            if (!wait_a_free(i, h)) break;
             tc_fence_after();
-            const float2 *stage = reinterpret_cast<const float2 *>(sm + kSmStage0 + b * kStageBytes);
-            const uint32_t lane_base = tmem + (uint32_t(32 * q) << 16) + uint32_t(b) * 256u;
+            const float2 *stage = reinterpret_cast<const float2 *>(sm + L::kStage0 + b * kStageBytes);
+            const uint32_t abase = abase_of(b, h) + (uint32_t(32 * q) << 16);
 #pragma unroll
             for (int ch = 0; ch < 2; ++ch) {  // 16 amplitudes (TMEM columns) at a time
-                uint32_t hi[16], lo[16];
+                float2 v[16];
 #pragma unroll
-                for (int jj = 0; jj < 16; ++jj) {
-                    const float2 v = stage[(32 * h + 16 * ch + jj) * M + srow];
-                    split_bf16x2(v, hi[jj], lo[jj]);
-                }
-                tmem_st16(lane_base + 128u + uint32_t(32 * h + 16 * ch), hi);
-                tmem_st16(lane_base + 192u + uint32_t(32 * h + 16 * ch), lo);
+                for (int jj = 0; jj < 16; ++jj) v[jj] = stage[(32 * h + 16 * ch + jj) * M + srow];
+                put16(abase, acol_in(h, ch), v);
             }
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(bar_full(b));
+            if (lane == 0) mbar_arrive(bar_full_h(b, h));
             if (i + 2 < my_tiles) issue(i + 2, b);
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
@@ -378,26 +485,22 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
         for (uint32_t i = 0; i < my_tiles; ++i) {
             const int b = i & 1;
             if (!warp_wait(bar_loaded(b), (i >> 1) & 1, abort_flag)) break;
-            if (i >= 2 && !warp_wait(bar_done(b), ((i >> 1) - 1) & 1, abort_flag)) break;
+            if (!wait_a_free(i, h)) break;
             tc_fence_after();
-            const float2 *stage = reinterpret_cast<const float2 *>(sm + kSmStage0 + b * kStageBytes);
+            const float2 *stage = reinterpret_cast<const float2 *>(sm + L::kStage0 + b * kStageBytes);
             const uint32_t csr = cs[srow];
-            const uint32_t lane_base = tmem + (uint32_t(32 * q) << 16) + uint32_t(b) * 256u;
+            const uint32_t abase = abase_of(b, h) + (uint32_t(32 * q) << 16);
 #pragma unroll
             for (int ch = 0; ch < 2; ++ch) {
-                uint32_t hi[16], lo[16];
+                float2 v[16];
 #pragma unroll
-                for (int jj = 0; jj < 16; ++jj) {
-                    const float2 v = stage[swz(uint32_t(cj[32 * h + 16 * ch + jj]) | csr)];
-                    split_bf16x2(v, hi[jj], lo[jj]);
-                }
-                tmem_st16(lane_base + 128u + uint32_t(32 * h + 16 * ch), hi);
-                tmem_st16(lane_base + 192u + uint32_t(32 * h + 16 * ch), lo);
+                for (int jj = 0; jj < 16; ++jj) v[jj] = stage[swz(uint32_t(cj[32 * h + 16 * ch + jj]) | csr)];
+                put16(abase, acol_in(h, ch), v);
             }
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(bar_full(b));
+            if (lane == 0) mbar_arrive(bar_full_h(b, h));
             // the other stage takes tile i+1 once tile i-1's outputs have been stored from
             // it (tiles 0 and 1 were issued up front); converting tile i first keeps its
             // MMA and epilogue running while tile i+1 is in flight
@@ -418,17 +521,13 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
             tc_fence_after();
             const uint64_t tile = uint64_t(blockIdx.x) + uint64_t(i) * gridDim.x;
             const uint64_t base = slice_base(tile * M + srow, t);
-            const uint32_t lane_base = tmem + (uint32_t(32 * q) << 16) + uint32_t(b) * 256u;
+            const uint32_t dbase = dcol_of(b) + (uint32_t(32 * q) << 16);
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
-                uint32_t v[32];
-                tmem_ld32(lane_base + uint32_t(64 * h + 32 * c), v);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                float2 v[16];
+                get16(dbase, 32 * h + 16 * c, v);
 #pragma unroll
-                for (int aa = 0; aa < 16; ++aa) {
-                    const int j = 32 * h + 16 * c + aa;
-                    a.psi[base | off[j]] = make_float2(__uint_as_float(v[2 * aa]), __uint_as_float(v[2 * aa + 1]));
-                }
+                for (int jj = 0; jj < 16; ++jj) a.psi[base | off[32 * h + 16 * c + jj]] = v[jj];
             }
             tc_fence_before();
             __syncwarp();
@@ -444,19 +543,14 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
             const int b = i & 1;
             if (!warp_wait(bar_done(b), (i >> 1) & 1, abort_flag)) break;
             tc_fence_after();
-            float2 *stage = reinterpret_cast<float2 *>(sm + kSmStage0 + b * kStageBytes);
-            const uint32_t lane_base = tmem + (uint32_t(32 * q) << 16) + uint32_t(b) * 256u;
+            float2 *stage = reinterpret_cast<float2 *>(sm + L::kStage0 + b * kStageBytes);
+            const uint32_t dbase = dcol_of(b) + (uint32_t(32 * q) << 16);
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
-                uint32_t v[32];
-                tmem_ld32(lane_base + uint32_t(64 * h + 32 * c), v);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                float2 v[16];
+                get16(dbase, 32 * h + 16 * c, v);
 #pragma unroll
-                for (int aa = 0; aa < 16; ++aa) {
-                    const int j = 32 * h + 16 * c + aa;
-                    stage[swz(uint32_t(cj[j]) | csr)] =
-                        make_float2(__uint_as_float(v[2 * aa]), __uint_as_float(v[2 * aa + 1]));
-                }
+                for (int jj = 0; jj < 16; ++jj) stage[swz(uint32_t(cj[32 * h + 16 * c + jj]) | csr)] = v[jj];
             }
             tc_fence_before();
             __syncwarp();
@@ -478,33 +572,69 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
     } else {
         // ---------------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            const uint32_t bhi = smem_u32(sm + kSmBhi), blo = smem_u32(sm + kSmBlo);
-            int64_t last = -1;
+            const uint32_t bimg = smem_u32(sm);
+            uint32_t last_bar = 0, last_par = 0;  // the most recent commit, for the drain
+            bool committed = false;
+            auto commit = [&](uint32_t bar, uint32_t par) {
+                mma_commit(bar);
+                last_bar = bar;
+                last_par = par;
+                committed = true;
+            };
             for (uint32_t i = 0; i < my_tiles; ++i) {
                 const int b = i & 1;
-                if (!mbar_wait(bar_full(b), (i >> 1) & 1, abort_flag)) break;
+                const uint32_t par = (i >> 1) & 1;
+                if (!mbar_wait(bar_full(b), par, abort_flag)) break;
                 if (i >= 2 && !mbar_wait(bar_free(b), ((i >> 1) - 1) & 1, abort_flag)) break;
                 tc_fence_after();
-                const uint32_t dcol = tmem + uint32_t(b) * 256u;
-                const uint32_t ahi = dcol + 128u, alo = dcol + 192u;
+                const uint32_t dcol = dcol_of(b), acol = acol_of(b);
+                if constexpr (kTf32) {
+                    // D[:, 0:64] += X_re Ur^T - X_im Ui^T and D[:, 64:128] += X_re Ui^T + X_im Ur^T:
+                    // B1 = [Ur; Ui] for the Re inputs, B2 = [-Ui; Ur] for the Im inputs, both
+                    // 128-row windows of one [-Ui; Ur; Ui] image per split.
+                    auto half = [&](int hh) {
 #pragma unroll
-                for (int kk = 0; kk < KR / 16; ++kk) {
-                    // K step kk covers reals [16 kk, 16 kk + 16): atom column kk / 4, 32-byte step kk % 4
-                    const uint32_t boff = uint32_t(kk >> 2) * uint32_t(NR * 128) + uint32_t(kk & 3) * 32u;
-                    const uint64_t dhi = sw128_desc(bhi + boff), dlo = sw128_desc(blo + boff);
-                    const uint32_t acol = uint32_t(kk) * 8u;  // 16 bf16 = 8 TMEM columns
-                    mma_bf16_tmemA(dcol, ahi + acol, dhi, kk > 0 ? 1u : 0u);
-                    mma_bf16_tmemA(dcol, alo + acol, dhi, 1u);
-                    mma_bf16_tmemA(dcol, ahi + acol, dlo, 1u);
+                        for (int k4 = 0; k4 < 4; ++k4) {
+                            const int kk = 4 * hh + k4;
+                            // K step kk covers inputs [8 kk, 8 kk + 8): atom column kk / 4, 32-byte step kk % 4
+                            const uint32_t kof = uint32_t(hh) * uint32_t(kTf32Atom) + uint32_t(k4) * 32u;
+                            const uint32_t hi = bimg + kof, lo = bimg + uint32_t(kTf32Split) + kof;
+                            const uint64_t b1h = sw128_desc(hi + 64u * 128u), b1l = sw128_desc(lo + 64u * 128u);
+                            const uint64_t b2h = sw128_desc(hi), b2l = sw128_desc(lo);
+                            // A columns of this K step: Re_hi, Re_lo (+32), Im_hi (+64), Im_lo (+96)
+                            const uint32_t ac = acol + 128u * uint32_t(hh) + uint32_t(k4) * 8u;
+                            mma_tf32_tmemA(dcol, ac, b1h, kIdescTf32, kk > 0 ? 1u : 0u);
+                            mma_tf32_tmemA(dcol, ac + 32u, b1h, kIdescTf32, 1u);
+                            mma_tf32_tmemA(dcol, ac, b1l, kIdescTf32, 1u);
+                            mma_tf32_tmemA(dcol, ac + 64u, b2h, kIdescTf32, 1u);
+                            mma_tf32_tmemA(dcol, ac + 96u, b2h, kIdescTf32, 1u);
+                            mma_tf32_tmemA(dcol, ac + 64u, b2l, kIdescTf32, 1u);
+                        }
+                    };
+                    half(0);
+                    commit(bar_done_a(b), par);
+                    if (!mbar_wait(bar_full1(b), par, abort_flag)) break;
+                    tc_fence_after();
+                    half(1);
+                } else {
+                    const uint32_t bhi = bimg + uint32_t(kSmBhi), blo = bimg + uint32_t(kSmBlo);
+#pragma unroll
+                    for (int kk = 0; kk < KR / 16; ++kk) {
+                        // K step kk covers reals [16 kk, 16 kk + 16): atom column kk / 4, 32-byte step kk % 4
+                        const uint32_t boff = uint32_t(kk >> 2) * uint32_t(NR * 128) + uint32_t(kk & 3) * 32u;
+                        const uint64_t dhi = sw128_desc(bhi + boff), dlo = sw128_desc(blo + boff);
+                        const uint32_t ac = acol + uint32_t(kk) * 8u;  // 16 bf16 = 8 TMEM columns
+                        mma_bf16_tmemA(dcol, ac, dhi, kk > 0 ? 1u : 0u);
+                        mma_bf16_tmemA(dcol, ac + 64u, dhi, 1u);
+                        mma_bf16_tmemA(dcol, ac, dlo, 1u);
+                    }
                 }
-                mma_commit(bar_done(b));
-                last = i;
+                commit(bar_done(b), par);
             }
-            if (*abort_flag && last >= 0) {
+            if (*abort_flag && committed) {
                 // drain: the last committed MMAs must finish before tensor memory is freed
                 const long long t0 = clock64();
-                while (!mbar_try_wait(bar_done(int(last & 1)), uint32_t((last >> 1) & 1)) &&
-                       clock64() - t0 < kWaitCycles) {
+                while (!mbar_try_wait(last_bar, last_par) && clock64() - t0 < kWaitCycles) {
                 }
             }
         }
@@ -536,7 +666,9 @@ static float bf16_to_float(uint16_t b) {
     return f;
 }
 
-size_t tc_ops_bytes() { return size_t(2 * tc::kOpBytes); }
+size_t tc_ops_bytes(bool tf32) {
+    return size_t(tf32 ? tc::Layout<true>::kBBytes : tc::Layout<false>::kBBytes);
+}
 
 // Byte offset of element (row n, k) in the K-major, 128-byte-swizzled image of a
 // 128 x 128 bf16 operand: two 64-element atom columns of 128 rows x 128 bytes;
@@ -547,10 +679,29 @@ static size_t sw128_offset(int n, int k) {
     return size_t(kc) * (tc::NR * 128) + size_t(n) * 128 + size_t(((chunk ^ (n & 7)) << 4) + byte);
 }
 
-void tc_build_ops(const Pass &p, void *host_image) {
+// The same for the 192 x 64 tf32 image: two 32-element atom columns of 192 rows.
+static size_t sw128_offset_tf32(int n, int k) {
+    const int kc = k >> 5, within = (k & 31) * 4;
+    const int chunk = within >> 4, byte = within & 15;
+    return size_t(kc) * tc::kTf32Atom + size_t(n) * 128 + size_t(((chunk ^ (n & 7)) << 4) + byte);
+}
+
+// Round to nearest (ties away from zero) at 10 stored mantissa bits, kept as an fp32
+// bit pattern with the low 13 bits clear: the tf32 value the tensor cores read.
+static uint32_t tf32_rna_bits(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return u & 0xffffe000u;  // Inf / NaN: truncate
+    return (u + 0x1000u) & 0xffffe000u;
+}
+static float bits_to_float(uint32_t u) {
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+static void build_ops_bf16(const Pass &p, uint8_t *img) {
     using namespace tc;
-    uint8_t *img = static_cast<uint8_t *>(host_image);
-    std::memset(img, 0, tc_ops_bytes());
     for (int oa = 0; oa < D; ++oa)
         for (int ib = 0; ib < D; ++ib) {
             const cd u = p.U[size_t(oa) * D + ib];
@@ -568,17 +719,49 @@ void tc_build_ops(const Pass &p, void *host_image) {
         }
 }
 
-int launch_pass_tc(void *psi, int n, const Pass &p, const void *d_ops, int *d_err, void *stream) {
+static void build_ops_tf32(const Pass &p, uint8_t *img) {
+    using namespace tc;
+    for (int oa = 0; oa < D; ++oa)
+        for (int ib = 0; ib < D; ++ib) {
+            const cd u = p.U[size_t(oa) * D + ib];
+            // rows 0..63: -Im U, rows 64..127: Re U, rows 128..191: Im U
+            const double v[3] = {-u.imag(), u.real(), u.imag()};
+            for (int blk = 0; blk < 3; ++blk) {
+                const uint32_t h = tf32_rna_bits(float(v[blk]));
+                const uint32_t l = tf32_rna_bits(float(v[blk] - double(bits_to_float(h))));
+                const size_t o = sw128_offset_tf32(blk * D + oa, ib);
+                std::memcpy(img + o, &h, 4);
+                std::memcpy(img + kTf32Split + o, &l, 4);
+            }
+        }
+}
+
+void tc_build_ops(const Pass &p, void *host_image, bool tf32) {
+    uint8_t *img = static_cast<uint8_t *>(host_image);
+    std::memset(img, 0, tc_ops_bytes(tf32));
+    if (tf32) build_ops_tf32(p, img);
+    else build_ops_bf16(p, img);
+}
+
+template <bool kStaged, bool kTf32>
+static int set_smem_attr() {
+    const cudaError_t e = cudaFuncSetAttribute(k_fused_tc<kStaged, kTf32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               tc::Layout<kTf32>::kAlloc);
+    return e == cudaSuccess ? RCS_OK : note_launch_error("tensor-core kernel shared-memory attribute", e);
+}
+
+int launch_pass_tc(void *psi, int n, const Pass &p, const void *d_ops, int *d_err, void *stream, bool tf32) {
     using namespace tc;
     if (p.k != K || n < K + 7) return RCS_ERR_UNSUPPORTED;
     static bool attr_done[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 64 && !attr_done[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmAlloc);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_fused_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmAlloc);
-        if (e != cudaSuccess) return note_launch_error("tensor-core kernel shared-memory attribute", e);
+        int rc = set_smem_attr<false, false>();
+        if (rc == RCS_OK) rc = set_smem_attr<true, false>();
+        if (rc == RCS_OK) rc = set_smem_attr<false, true>();
+        if (rc == RCS_OK) rc = set_smem_attr<true, true>();
+        if (rc != RCS_OK) return rc;
         attr_done[dev] = true;
     }
     TcArgs a;
@@ -606,10 +789,14 @@ int launch_pass_tc(void *psi, int n, const Pass &p, const void *d_ops, int *d_er
     int low = 0;
     for (int i = 0; i < K; ++i) low += p.t[i] < 5;
     const bool staged = low >= 4;
-    if (staged)
-        k_fused_tc<true><<<grid, kThreads, kSmAlloc, static_cast<cudaStream_t>(stream)>>>(a);
-    else
-        k_fused_tc<false><<<grid, kThreads, kSmAlloc, static_cast<cudaStream_t>(stream)>>>(a);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (tf32) {
+        if (staged) k_fused_tc<true, true><<<grid, kThreads, Layout<true>::kAlloc, st>>>(a);
+        else k_fused_tc<false, true><<<grid, kThreads, Layout<true>::kAlloc, st>>>(a);
+    } else {
+        if (staged) k_fused_tc<true, false><<<grid, kThreads, Layout<false>::kAlloc, st>>>(a);
+        else k_fused_tc<false, false><<<grid, kThreads, Layout<false>::kAlloc, st>>>(a);
+    }
     return launch_status("tensor-core pass");
 }
 

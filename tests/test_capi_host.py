@@ -59,7 +59,8 @@ def _plan_passes(plan):
 
 @pytest.mark.parametrize("precision,kmax,n", [(capi.RCS_PREC_FP32_FUSED, 2, 10), (capi.RCS_PREC_FP32_FUSED, 4, 10),
                                               (capi.RCS_PREC_FP32_FUSED, 5, 9), (capi.RCS_PREC_BF16X3, 0, 13),
-                                              (capi.RCS_PREC_FP32_FUSED, 4, 14), (capi.RCS_PREC_FP32_PLAIN, 0, 9)])
+                                              (capi.RCS_PREC_FP32_FUSED, 4, 14), (capi.RCS_PREC_FP32_PLAIN, 0, 9),
+                                              (capi.RCS_PREC_TF32X3, 0, 14)])
 def test_fused_plan_reproduces_circuit(oracle, lib, precision, kmax, n):
     """Applying the planned passes (FP64 matrices) with the oracle equals applying
     the circuit gate by gate with the oracle."""
@@ -87,7 +88,7 @@ def test_fused_plan_reproduces_circuit(oracle, lib, precision, kmax, n):
     assert info["n_gates"] == len(circ.gates)
     if precision == capi.RCS_PREC_FP32_PLAIN:
         assert info["n_passes"] == len(circ.gates)
-    elif precision == capi.RCS_PREC_BF16X3:
+    elif precision in (capi.RCS_PREC_BF16X3, capi.RCS_PREC_TF32X3):
         assert all(len(t) == 6 for t, _ in passes)
     else:
         assert max(len(t) for t, _ in passes) <= kmax

@@ -6,7 +6,8 @@ tests check properties that hold at any size:
   * echo: the circuit followed by its inverse returns |0...0> (normalised overlap
     >= 1 - 1e-5);
   * the tensor-core BF16x3 state and an FP32 state agree on a seeded subset of
-    ~2^20 amplitudes: subset infidelity <= 1e-5;
+    ~2^20 amplitudes: subset infidelity <= 1e-5; so does the TF32x3 state, and it
+    lies closer to the FP32 state than the BF16x3 one does;
   * the norm stays 1 within the stated drift (FP32: 1e-5; BF16x3: 2e-6 per pass);
   * the XEB of the shots drawn from the BF16x3 state, scored by that state and by
     the FP32 state, agrees within 0.005; the FP32 state's own shots score near the
@@ -88,5 +89,12 @@ def test_full_size_workload(lib, name, cross):
         x_fp = capi.rcs_sample(ctx, shots, seed=12)
         F_fp = capi.rcs_xeb(ctx, x_fp)
         assert abs(F_fp - 1) <= 0.05 and abs(F_tc - 1) <= 0.05, (F_tc, F_fp)
+        # the TF32x3 tensor-core path
+        p_tf = run_plan(ctx, n, circ.gates, capi.RCS_PREC_TF32X3)
+        assert p_tf == p_tc
+        assert abs(capi.rcs_norm(ctx) - 1) <= NORM_DRIFT_PER_TC_PASS * p_tf
+        a_tf = capi.rcs_amplitudes(ctx, S)
+        inf_tf, inf_bf = subset_infidelity(a_tf, a_fp), subset_infidelity(a_tc, a_fp)
+        assert inf_tf <= 1e-5 and inf_tf < inf_bf, (inf_tf, inf_bf)
     finally:
         capi.rcs_destroy(ctx)
