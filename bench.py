@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--qubits", type=int, default=None,
                     help="profiling size: a circuit of the same family (20 cycles, ABCDCDAB) on a grid of this "
                          "many qubits instead of the named workload")
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32x3"],
+                    help="split precision of the tensor-core passes (bf16x3: the headline path)")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP32 plain/fused comparison runs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     return ap.parse_args()
@@ -279,8 +281,11 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    ctx = capi.rcs_create(circ.grid, capi.RCS_PREC_BF16X3, stream=sh)
-    plan = capi.rcs_plan_build(n, circ.gates, capi.RCS_PREC_BF16X3)
+    prec = capi.PRECISIONS[args.precision]
+    other = "tf32x3" if args.precision == "bf16x3" else "bf16x3"
+    ops_bytes = 65536 if args.precision == "bf16x3" else 98304  # operand image per tensor-core pass
+    ctx = capi.rcs_create(circ.grid, prec, stream=sh)
+    plan = capi.rcs_plan_build(n, circ.gates, prec)
     info = capi.rcs_plan_info(plan)
     capi.rcs_plan_upload(ctx, plan)
     d_bits = torch.empty(shots, dtype=torch.int64, device="cuda")
@@ -359,22 +364,22 @@ def main():
         xs = capi.rcs_sample(ctx, shots, 77 + s)
         F_e2e = capi.rcs_xeb(ctx, xs)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    h2d = circ.gates.nbytes + passes * 65536 + shots * 8
+    h2d = circ.gates.nbytes + passes * ops_bytes + shots * 8
     d2h = shots * 8 + 8
 
     compare = {}
     if not args.no_compare:
-        # same circuit through the plain FP32 per-gate path, the fused FP32 path and the TF32x3
-        # tensor-core path (one run each), and the subset infidelity of each tensor-core state
-        # against the fused FP32 state on a seeded 2^20-amplitude subset
+        # same circuit through the plain FP32 per-gate path, the fused FP32 path and the other
+        # tensor-core split (one run each), and the subset infidelity of each state against the
+        # fused FP32 state on a seeded 2^20-amplitude subset
         rng = np.random.default_rng(2**20)
         subset = np.unique(rng.integers(0, 1 << n, size=1 << 20, dtype=np.uint64))
         capi.rcs_reset(ctx)
         capi.rcs_plan_run(ctx, plan)
-        amps = {"bf16x3": capi.rcs_amplitudes(ctx, subset)}
-        for name, prec, kmax in (("fp32_plain", capi.RCS_PREC_FP32_PLAIN, 0), ("fp32_fused_k4", capi.RCS_PREC_FP32_FUSED, 4),
-                                 ("tf32x3", capi.RCS_PREC_TF32X3, 0)):
-            p2 = capi.rcs_plan_build(n, circ.gates, prec, kmax)
+        amps = {args.precision: capi.rcs_amplitudes(ctx, subset)}
+        for name, p2prec, kmax in (("fp32_plain", capi.RCS_PREC_FP32_PLAIN, 0),
+                                   ("fp32_fused_k4", capi.RCS_PREC_FP32_FUSED, 4), (other, capi.PRECISIONS[other], 0)):
+            p2 = capi.rcs_plan_build(n, circ.gates, p2prec, kmax)
             i2 = capi.rcs_plan_info(p2)
             capi.rcs_plan_upload(ctx, p2)
             capi.rcs_reset(ctx)
@@ -396,8 +401,8 @@ def main():
         ref = amps["fp32_fused_k4"]
         compare["subset_infidelity_vs_fp32_fused_k4"] = {k: subset_infidelity(amps[k], ref)
                                                          for k in ("bf16x3", "tf32x3", "fp32_plain")}
-        compare["bf16x3_apply_s"] = statistics.median(apply_ms) / 1e3
-        compare["speedup_vs_fp32_plain"] = compare["fp32_plain"]["apply_s"] / compare["bf16x3_apply_s"]
+        compare[f"{args.precision}_apply_s"] = statistics.median(apply_ms) / 1e3
+        compare["speedup_vs_fp32_plain"] = compare["fp32_plain"]["apply_s"] / compare[f"{args.precision}_apply_s"]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -411,12 +416,13 @@ def main():
             "metric": METRIC, "value": per_circuit_seconds(ms_step, world), "unit": "s", "n_gpus": world,
             "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16x3 (fp32 accumulate); fp32 state; exact fixed-point/f64 reductions",
+            "vs_baseline": None,
+            "dtype": f"{args.precision} (fp32 accumulate); fp32 state; exact fixed-point/f64 reductions",
             "data": "synthetic",
             "config": {"workload": args.workload, "qubits": n, "cycles": circ.cycles, "pattern": circ.pattern,
                        "grid": f"{circ.grid.rows}x{circ.grid.cols}-{len(circ.grid.removed)}", "shots": shots,
                        "gates": len(circ.gates), "passes": passes, "prefix_passes_on_substate": prefix,
-                       "prefix_qubits": int(info["prefix_qubits"]), "precision": "bf16x3",
+                       "prefix_qubits": int(info["prefix_qubits"]), "precision": args.precision,
                        "state_bytes": 8 * 2**n, "l2": (f"inputs larger than L2 (state {8 * 2**n / 2**30:.0f} GiB > 129 MB)" if 8 * 2**n > 129e6
                               else "state fits in L2: no flush between steps"),
                        "parallelism": f"replicas{world}" if world > 1 else "single"},

@@ -515,6 +515,17 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
         const int e = warp - kLoaderWarps;
         const int q = e & 3, h = e >> 2;
         const int srow = 32 * q + lane;
+        // Lowest target on index bit 0: the thread writes amplitudes j and j+1 of its slice
+        // (adjacent) as one 16-byte store. On bit 1: index bit 0 is the lowest slice bit, and
+        // lane pairs swap one amplitude so that each lane writes two adjacent slices of one j
+        // (the even lane j, the odd lane j+1). Either way a store instruction covers 512
+        // contiguous bytes; otherwise 8-byte stores already fill whole 32-byte sectors.
+        const int smode = t[0] == 0 ? 1 : (t[0] == 1 ? 2 : 0);
+        const bool odd = lane & 1;
+        auto st16 = [](float2 *p, float2 x, float2 y) {
+            asm volatile("st.global.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(x.x), "f"(x.y), "f"(y.x), "f"(y.y)
+                         : "memory");
+        };
         for (uint32_t i = 0; i < my_tiles; ++i) {
             const int b = i & 1;
             if (!warp_wait(bar_done(b), (i >> 1) & 1, abort_flag)) break;
@@ -526,8 +537,25 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
             for (int c = 0; c < 2; ++c) {
                 float2 v[16];
                 get16(dbase, 32 * h + 16 * c, v);
+                const int j0 = 32 * h + 16 * c;
+                if (smode == 1) {
 #pragma unroll
-                for (int jj = 0; jj < 16; ++jj) a.psi[base | off[32 * h + 16 * c + jj]] = v[jj];
+                    for (int jj = 0; jj < 16; jj += 2) st16(a.psi + (base | off[j0 + jj]), v[jj], v[jj + 1]);
+                } else if (smode == 2) {
+                    const uint64_t pbase = base & ~1ull;  // the even slice of the lane pair
+#pragma unroll
+                    for (int jj = 0; jj < 16; jj += 2) {
+                        // selects, not branches: one 16-byte store instruction for the whole warp
+                        const float2 send = odd ? v[jj] : v[jj + 1];
+                        const float2 recv = make_float2(__shfl_xor_sync(0xffffffffu, send.x, 1),
+                                                        __shfl_xor_sync(0xffffffffu, send.y, 1));
+                        const float2 x = odd ? recv : v[jj], y = odd ? v[jj + 1] : recv;
+                        st16(a.psi + (pbase | off[j0 + jj + (odd ? 1 : 0)]), x, y);
+                    }
+                } else {
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) a.psi[base | off[j0 + jj]] = v[jj];
+                }
             }
             tc_fence_before();
             __syncwarp();
