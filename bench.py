@@ -29,10 +29,11 @@ sys.path.insert(0, ROOT)
 from paper_2512_07311_gb300 import circuits as C  # noqa: E402
 
 METRIC = "34q 20-cycle circuit time (s), shots/s; fused-TC vs plain FP32 at 1e-5 infid"
-# DRAM bytes (read + write) per amplitude per tensor-core pass, from an ncu capture of the pass
-# on a 2^27-amplitude state (2.087 GB per launch); the traffic of a pass is proportional to the
-# state size, so a launch at n qubits moves this x 2^n.
-TC_DRAM_BYTES_PER_AMP = 2.087e9 / 2**27
+# DRAM bytes (read + write) per amplitude per tensor-core pass, from ncu captures of full passes
+# on a 2^27-amplitude state (BF16x3: mean of seven passes, 2.089 GB per launch; TF32x3: two passes,
+# 2.0915 GB); the traffic of a pass is proportional to the state size, so a launch at n qubits moves
+# this x 2^n.
+TC_DRAM_BYTES_PER_AMP = {"bf16x3": 2.089e9 / 2**27, "tf32x3": 2.0915e9 / 2**27}
 WORKLOAD = "34q_5x7m1_20cyc"
 
 
@@ -205,38 +206,72 @@ def run_reference(args, rank: int, world: int):
 # ------------------------------------------------------------------ our arm
 
 def run_batch(args, torch, capi):
-    """64 seeded circuits (16-26 qubits, 10-20 cycles, 10^5 shots each) in one graph launch:
-    reset, persistent fused apply, per-circuit sampling and XEB."""
+    """64 seeded circuits (16-26 qubits, 10-20 cycles, 10^5 shots each) in one graph launch.
+    The tensor-core engine (one launch chain per circuit: fused 6-qubit passes with each
+    circuit's own layout and sub-state prefix, then sampling and XEB) is the line's value;
+    the persistent FP32 engine (every pass of every circuit as items of one cooperative
+    launch, fusion width autotuned) is timed beside it in `compare`."""
     circs = C.batch_workload(64, 1000)
     shots = args.shots or 100_000
     stream = torch.cuda.current_stream()
-    b = capi.rcs_batch_create([(c.n_qubits, c.gates, shots, c.seed) for c in circs])
-    infos = [capi.rcs_batch_info(b, i) for i in range(len(circs))]
-    for _ in range(args.warmup):
-        capi.rcs_batch_launch(b, stream.cuda_stream)
-    capi.rcs_batch_wait(b, stream.cuda_stream)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(args.steps):
-        capi.rcs_batch_launch(b, stream.cuda_stream)
-    e1.record(stream)
-    capi.rcs_batch_wait(b, stream.cuda_stream)
-    ms = e0.elapsed_time(e1) / args.steps
-    xebs = [capi.rcs_batch_result(b, i, 0)[1] for i in range(len(circs))]
-    capi.rcs_batch_destroy(b)
-    apply_bytes = sum(16.0 * 2**inf["n_qubits"] * inf["n_passes"] for inf in infos)
     peaks = measured_peaks()
+
+    def timed(precision):
+        b = capi.rcs_batch_create([(c.n_qubits, c.gates, shots, c.seed) for c in circs], precision=precision)
+        infos = [capi.rcs_batch_info(b, i) for i in range(len(circs))]
+        for _ in range(args.warmup):
+            capi.rcs_batch_launch(b, stream.cuda_stream)
+        capi.rcs_batch_wait(b, stream.cuda_stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            capi.rcs_batch_launch(b, stream.cuda_stream)
+        e1.record(stream)
+        capi.rcs_batch_wait(b, stream.cuda_stream)
+        ms = e0.elapsed_time(e1) / args.steps
+        xebs = [capi.rcs_batch_result(b, i, 0)[1] for i in range(len(circs))]
+        capi.rcs_batch_destroy(b)
+        return ms, infos, xebs
+
+    def state_bytes(precision, infos):
+        """HBM bytes of state construction: passes (the sub-state prefix at its own size), reset/expansion."""
+        total = 0.0
+        for c, inf in zip(circs, infos):
+            n = c.n_qubits
+            if precision == capi.RCS_PREC_FP32_FUSED:
+                total += 16.0 * 2**n * inf["n_passes"] + 8.0 * 2**n
+                continue
+            plan = capi.rcs_plan_build(n, c.gates, precision)
+            pi = capi.rcs_plan_info(plan)
+            capi.rcs_plan_destroy(plan)
+            pre, m = pi["prefix_passes"], pi["prefix_qubits"]
+            total += 16.0 * 2**n * (pi["n_passes"] - pre) + 16.0 * 2**m * pre + 8.0 * 2**n + (8.0 * 2**m if pre else 0)
+        return total
+
+    prec = capi.PRECISIONS[args.precision]
+    ms, infos, xebs = timed(prec)
+    apply_bytes = state_bytes(prec, infos)
+    sample_bytes = sum(16.0 * 2**c.n_qubits for c in circs)  # block sums + the sampled blocks, about two reads
+    ms_f, infos_f, xebs_f = timed(capi.RCS_PREC_FP32_FUSED)
+    bytes_f = state_bytes(capi.RCS_PREC_FP32_FUSED, infos_f)
     line = {"metric": "64-circuit batched workload time (s)", "value": ms / 1e3, "unit": "s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": False, "data": "synthetic",
-            "config": {"workload": "batch64", "circuits": len(circs),
+            "higher_is_better": False, "data": "synthetic", "dtype": f"{args.precision} (fp32 accumulate); fp32 state",
+            "config": {"workload": "batch64", "circuits": len(circs), "engine": "tensor-core launch chains",
                        "qubits": [c.n_qubits for c in circs], "shots_per_circuit": shots,
-                       "k_chosen": [inf["k"] for inf in infos], "passes": [inf["n_passes"] for inf in infos]},
-            "apply_hbm_bytes": apply_bytes,
-            "apply_plus_sampling_GBps": apply_bytes / (ms / 1e3) / 1e9,
-            "frac_of_hbm_if_all_apply": apply_bytes / (ms / 1e3) / 1e9 / peaks["hbm_gbs"],
-            "xeb_mean": float(np.mean(xebs)), "xeb_min": float(np.min(xebs)), "xeb_max": float(np.max(xebs))}
+                       "k": [inf["k"] for inf in infos], "passes": [inf["n_passes"] for inf in infos],
+                       "l2": "states of 16-26 qubits: the largest (512 MiB) exceed L2; no flush between steps"},
+            "state_hbm_bytes": apply_bytes,
+            "state_plus_sampling_GBps": (apply_bytes + sample_bytes) / (ms / 1e3) / 1e9,
+            "frac_of_hbm": (apply_bytes + sample_bytes) / (ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+            "xeb_mean": float(np.mean(xebs)), "xeb_min": float(np.min(xebs)), "xeb_max": float(np.max(xebs)),
+            "compare": {"fp32_persistent": {
+                "value": ms_f / 1e3, "k_chosen": [inf["k"] for inf in infos_f],
+                "passes_total": int(sum(inf["n_passes"] for inf in infos_f)), "state_hbm_bytes": bytes_f,
+                "frac_of_hbm": (bytes_f + sample_bytes) / (ms_f / 1e3) / 1e9 / peaks["hbm_gbs"],
+                "xeb_mean": float(np.mean(xebs_f))},
+                "speedup_vs_fp32_persistent": ms_f / ms}}
     print(json.dumps(line), flush=True)
 
 
@@ -348,7 +383,7 @@ def main():
     bytes_per_launch = 16.0 * 2.0**n
     achieved = bytes_per_launch / t_pass_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": TC_DRAM_BYTES_PER_AMP * 2.0**n,
+                "frac": achieved / peaks["hbm_gbs"], "traffic": TC_DRAM_BYTES_PER_AMP[args.precision] * 2.0**n,
                 "traffic_src": "ncu capture at 27 qubits scaled by 2^(n-27)",
                 "kernel": "k_fused_tc", "peak_src": peaks["src"],
                 "algorithmic_bytes_per_launch": bytes_per_launch, "launches_per_step": full_passes,

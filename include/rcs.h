@@ -279,11 +279,20 @@ typedef struct {
     uint64_t seed;
 } rcs_batch_item;
 
-/* Builds a batch: allocates every state and sampler buffer, plans every circuit
- * (FP32 fused passes; opts->k_max in 2..5 fixes the fusion width, 0 or
- * opts->autotune = 1 lets timed trials of the batched kernel choose it per qubit
- * count, cached for the process), uploads the work tables and captures the graph.
- * opts may be NULL (autotune). Synchronous. */
+/* Builds a batch: allocates every state and sampler buffer, plans every circuit,
+ * uploads what the kernels need and captures the graph. Synchronous.
+ * Engine, by opts->precision:
+ *   FP32_FUSED (or FP32_PLAIN, or opts NULL): every pass of every circuit is an item
+ *     list of one persistent kernel launch. The passes are FP32 fused; opts->k_max in
+ *     2..5 fixes the fusion width, while 0 or opts->autotune = 1 lets timed trials of
+ *     the batched kernel choose it per qubit count, cached for the process.
+ *   BF16X3 or TF32X3: every circuit is planned like rcs_apply_circuit on a fresh
+ *     state (fused 6-qubit tensor-core passes, its own qubit layout and sub-state
+ *     prefix; circuits under 13 qubits get FP32 fused passes). The graph holds one
+ *     chain of launches per circuit on up to 32 parallel branches. opts->k_max must
+ *     be 0 or 6.
+ * Samples, XEB and rcs_batch_state_read use each circuit's own qubit numbering in
+ * either engine. */
 int rcs_batch_create(const rcs_batch_item *items, size_t n_items, const rcs_opts *opts, rcs_batch **out);
 
 /* Launches the batch's graph on `stream` (cudaStream_t): reset every state to
@@ -306,10 +315,11 @@ int rcs_batch_result(rcs_batch *batch, size_t i, uint64_t *out_bits, double *out
 /* Copies amplitudes [first, first+count) of circuit i's state to host floats. */
 int rcs_batch_state_read(rcs_batch *batch, size_t i, uint64_t first, uint64_t count, float *out_re_im);
 
-/* Test hook for the bounded waits: work item skip_item (>= 0) never publishes its
- * completion, so the passes after it wait until wait_limit_s and the launch ends
- * with RCS_ERR_TIMEOUT; skip_item = -1 restores normal operation (limit ~2 s by
- * default). Recaptures the graph. */
+/* Test hook for the bounded waits of the persistent FP32 engine: work item
+ * skip_item (>= 0) never publishes its completion, so the passes after it wait until
+ * wait_limit_s and the launch ends with RCS_ERR_TIMEOUT; skip_item = -1 restores
+ * normal operation (limit ~2 s by default). Recaptures the graph. The tensor-core
+ * engine has no work items: RCS_ERR_UNSUPPORTED. */
 int rcs_batch_set_fault(rcs_batch *batch, int64_t skip_item, double wait_limit_s);
 
 /* Last error message of the batch. */

@@ -321,8 +321,9 @@ def rcs_xeb_static(d_state: int, n_qubits: int, d_samples: int, count: int, d_ou
 
 # ------------------------------------------------------------------ batched circuits
 
-def rcs_batch_create(items, k_max: int = 0, autotune: int = 1):
-    """items: iterable of (n_qubits, gates GATE_DTYPE array, shots, seed)."""
+def rcs_batch_create(items, k_max: int = 0, autotune: int = 1, precision: int = RCS_PREC_FP32_FUSED):
+    """items: iterable of (n_qubits, gates GATE_DTYPE array, shots, seed). precision
+    RCS_PREC_BF16X3 / RCS_PREC_TF32X3 selects the tensor-core engine (k_max 0 or 6)."""
     items = list(items)
     arr = (rcs_batch_item * len(items))()
     keep = []
@@ -334,7 +335,7 @@ def rcs_batch_create(items, k_max: int = 0, autotune: int = 1):
         slot.n_gates = len(k[0])
         slot.shots = shots
         slot.seed = seed
-    o = _opts(RCS_PREC_FP32_FUSED, k_max, 0, autotune)
+    o = _opts(precision, k_max, 0, autotune)
     out = _P()
     _check(load().rcs_batch_create(arr, len(items), ctypes.byref(o), ctypes.byref(out)))
     return out

@@ -262,15 +262,6 @@ BitMap to_stored(const rcs_ctx *c) {
     return m;
 }
 
-// stored index -> caller's basis index
-BitMap to_caller(const rcs_ctx *c) {
-    BitMap m = identity_map(c->n);
-    if (layout_identity(c)) return m;
-    m.identity = 0;
-    for (int q = 0; q < c->n; ++q) m.to[c->phys_of[q]] = uint8_t(q);
-    return m;
-}
-
 // Brings the stored state back to the identity layout with exact swap passes
 // (entries 0 and 1, so FP32 moves the amplitudes unchanged).
 int restore_layout(rcs_ctx *c) {
@@ -392,7 +383,7 @@ int run_passes(rcs_ctx *c, const Plan &plan, const uint8_t *d_ops, bool from_zer
 int ensure_sums(rcs_ctx *c) {
     if (c->sums_valid) return RCS_OK;
     if (int rc = materialize(c); rc != RCS_OK) return rc;
-    int rc = launch_block_sums(c->psi, c->n, c->bsum, c->d_err, c->stream);
+    int rc = launch_block_sums(c->psi, c->n, c->bsum, c->d_err, to_stored(c), c->stream);
     if (rc == RCS_OK) rc = launch_block_scan(c->bsum, c->bpre, c->chunk, c->total, c->n, c->d_err, c->stream);
     if (rc != RCS_OK) return fail(c, rc, "reduction launch failed: " + take_launch_error());
     c->sums_valid = true;
@@ -423,6 +414,23 @@ std::string take_launch_error() {
 int set_thread_error(int code, const std::string &msg) {
     g_err = msg;
     return code;
+}
+
+int plan_fresh_circuit(int n, const std::vector<HostGate> &gates, const rcs_opts &o, Plan *plan,
+                       std::vector<uint8_t> *images) {
+    const int rc = build_plan(nullptr, n, gates, o, plan, true);
+    if (rc == RCS_OK) build_ops_images(*plan, images);
+    return rc;
+}
+
+Pass substate_pass(const Pass &p, uint64_t T) { return compact_pass(p, T); }
+
+BitMap plan_to_stored(const Plan &plan) {
+    BitMap m = identity_map(plan.n);
+    if (plan.phys_of.empty()) return m;
+    m.identity = 0;
+    for (int q = 0; q < plan.n; ++q) m.to[q] = uint8_t(plan.phys_of[q]);
+    return m;
 }
 
 int device_sm_count() {
@@ -892,7 +900,7 @@ int rcs_sample_device(rcs_ctx *c, uint64_t shots, uint64_t seed, uint64_t *d_out
     if (!d_out_bits) return fail(c, RCS_ERR_ARG, "null output");
     int rc = ensure_sums(c);
     if (rc != RCS_OK) return rc;
-    if (launch_sample(c->psi, c->n, c->bsum, c->bpre, c->total, shots, seed, d_out_bits, to_caller(c), c->stream) !=
+    if (launch_sample(c->psi, c->n, c->bsum, c->bpre, c->total, shots, seed, d_out_bits, to_stored(c), c->stream) !=
         RCS_OK)
         return fail(c, RCS_ERR_CUDA, "sampler launch: " + take_launch_error());
     return RCS_OK;

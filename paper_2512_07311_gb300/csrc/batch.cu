@@ -18,9 +18,19 @@
 // st.global.cg (L2, never a stale L1 line from an earlier pass); a CTA publishes
 // its stores with a fence before its counter increment, and a waiting CTA fences
 // after seeing the count.
+//
+// Tensor-core engine (precision BF16X3 or TF32X3). Each circuit is planned like a
+// single one (fused 6-qubit passes, its own qubit layout and sub-state prefix), and the
+// graph holds one chain of launches per circuit -- reset or prefix and expansion, the
+// tensor-core passes, then the sampler and XEB -- on up to 32 parallel branches. A
+// tensor-core pass needs a whole SM (one 17-warp CTA with ~200 KB of shared memory
+// and 512 tensor-memory columns), so the passes of different circuits cannot share one
+// persistent kernel the way the FP32 items do; the graph's branches let the passes of
+// small circuits run side by side on the SMs the large ones leave free.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <bit>
 #include <chrono>
 #include <cmath>
 #include <map>
@@ -196,6 +206,11 @@ struct InstHost {
     uint64_t shots = 0, seed = 0;
     int k = 0;
     Plan plan;
+    // tensor-core engine: operand images, sub-state prefix, layout maps
+    uint8_t *d_ops = nullptr;
+    float2 *d_sub = nullptr;
+    int prefix = 0;
+    uint64_t tmask = 0;
     float2 *psi = nullptr;
     uint64_t *bsum = nullptr, *bpre = nullptr, *chunk = nullptr, *total = nullptr;
     uint64_t *d_bits = nullptr;  // shots
@@ -211,6 +226,7 @@ std::map<std::pair<int, int>, int> g_tuned;  // (device, n) -> k
 
 struct rcs_batch {
     int dev = 0;
+    bool tc = false;  // tensor-core engine (one launch chain per circuit)
     std::vector<InstHost> inst;
     BInst *d_inst = nullptr;
     BPass *d_pass = nullptr;
@@ -440,6 +456,8 @@ void free_batch(rcs_batch *b) {
         cudaFree(h.total);
         cudaFree(h.d_bits);
         cudaFree(h.d_xeb);
+        cudaFree(h.d_ops);
+        cudaFree(h.d_sub);
     }
     cudaFree(b->d_inst);
     cudaFree(b->d_pass);
@@ -451,9 +469,76 @@ void free_batch(rcs_batch *b) {
     delete b;
 }
 
+int launch_sampling(rcs_batch *b, InstHost &h, cudaStream_t st) {
+    if (h.shots == 0) return RCS_OK;
+    int rc;
+    if ((rc = launch_block_sums(h.psi, h.n, h.bsum, b->d_err, plan_to_stored(h.plan), st)) != RCS_OK ||
+        (rc = launch_block_scan(h.bsum, h.bpre, h.chunk, h.total, h.n, b->d_err, st)) != RCS_OK ||
+        (rc = launch_sample(h.psi, h.n, h.bsum, h.bpre, h.total, h.shots, h.seed, h.d_bits, plan_to_stored(h.plan),
+                            st)) != RCS_OK ||
+        (rc = launch_xeb(h.psi, h.n, h.d_bits, h.shots, h.total, h.d_xeb + 1, h.d_xeb, plan_to_stored(h.plan), st)) !=
+            RCS_OK)
+        return bfail(b, rc, "sampling launch: " + take_launch_error());
+    return RCS_OK;
+}
+
+int launch_pass(rcs_batch *b, const InstHost &h, float2 *psi, int n, const Pass &p, size_t i, cudaStream_t st) {
+    switch (p.kind) {
+        case PASS_1Q:
+        case PASS_2Q: return launch_pass_plain(psi, n, p, st);
+        case PASS_SIMT: return launch_pass_simt(psi, n, p, st);
+        case PASS_TC:
+            return launch_pass_tc(psi, n, p, h.d_ops + h.plan.tc_offset[i], b->d_err, st,
+                                  h.plan.precision == RCS_PREC_TF32X3);
+        default: return RCS_ERR_ARG;
+    }
+}
+
+// One circuit of the tensor-core engine: |0...0> (through the sub-state prefix when the
+// plan has one), every pass, then the sampler and XEB.
+int record_chain(rcs_batch *b, InstHost &h, cudaStream_t st) {
+    size_t first = 0;
+    int rc = RCS_OK;
+    if (h.prefix > 0) {
+        const int m = std::popcount(h.tmask);
+        if ((rc = launch_init_zero(h.d_sub, m, st)) != RCS_OK) return bfail(b, rc, "sub-state reset: " + take_launch_error());
+        for (int i = 0; i < h.prefix; ++i)
+            if ((rc = launch_pass(b, h, h.d_sub, m, substate_pass(h.plan.passes[size_t(i)], h.tmask), size_t(i), st)) !=
+                RCS_OK)
+                return bfail(b, rc, "sub-state pass: " + take_launch_error());
+        if ((rc = launch_expand(h.psi, h.n, h.d_sub, h.tmask, st)) != RCS_OK)
+            return bfail(b, rc, "expansion: " + take_launch_error());
+        first = size_t(h.prefix);
+    } else if ((rc = launch_init_zero(h.psi, h.n, st)) != RCS_OK) {
+        return bfail(b, rc, "reset: " + take_launch_error());
+    }
+    for (size_t i = first; i < h.plan.passes.size(); ++i)
+        if ((rc = launch_pass(b, h, h.psi, h.n, h.plan.passes[i], i, st)) != RCS_OK)
+            return bfail(b, rc, "pass launch: " + take_launch_error());
+    return launch_sampling(b, h, st);
+}
+
+int record_tc(rcs_batch *b) {
+    cudaStream_t s0 = b->cap;
+    BCUDA(b, cudaEventRecord(b->ev[0], s0), "fork event");
+    for (size_t j = 0; j < b->side.size(); ++j) BCUDA(b, cudaStreamWaitEvent(b->side[j], b->ev[0], 0), "fork");
+    // largest circuits first, so that the small ones fill in behind them
+    std::vector<size_t> order(b->inst.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return b->inst[x].n > b->inst[y].n; });
+    for (size_t r = 0; r < order.size(); ++r)
+        if (int rc = record_chain(b, b->inst[order[r]], b->side[r % b->side.size()]); rc != RCS_OK) return rc;
+    for (size_t j = 0; j < b->side.size(); ++j) {
+        BCUDA(b, cudaEventRecord(b->ev[1 + j], b->side[j]), "join event");
+        BCUDA(b, cudaStreamWaitEvent(s0, b->ev[1 + j], 0), "join");
+    }
+    return RCS_OK;
+}
+
 // Records the whole batch on b->cap: reset, persistent apply, then per circuit the
 // sampler and XEB kernels spread over side streams.
 int record(rcs_batch *b) {
+    if (b->tc) return record_tc(b);
     cudaStream_t s0 = b->cap;
     BCUDA(b, cudaMemsetAsync(b->d_next, 0, 8, s0), "clear work counter");
     BCUDA(b, cudaMemsetAsync(b->d_done, 0, b->inst.size() * sizeof(unsigned int), s0), "clear completion counters");
@@ -465,18 +550,8 @@ int record(rcs_batch *b) {
     if (rc != RCS_OK) return bfail(b, rc, take_launch_error());
     BCUDA(b, cudaEventRecord(b->ev[0], s0), "fork event");
     for (size_t j = 0; j < b->side.size(); ++j) BCUDA(b, cudaStreamWaitEvent(b->side[j], b->ev[0], 0), "fork");
-    for (size_t i = 0; i < b->inst.size(); ++i) {
-        InstHost &h = b->inst[i];
-        cudaStream_t st = b->side[i % b->side.size()];
-        if (h.shots == 0) continue;
-        if ((rc = launch_block_sums(h.psi, h.n, h.bsum, b->d_err, st)) != RCS_OK ||
-            (rc = launch_block_scan(h.bsum, h.bpre, h.chunk, h.total, h.n, b->d_err, st)) != RCS_OK ||
-            (rc = launch_sample(h.psi, h.n, h.bsum, h.bpre, h.total, h.shots, h.seed, h.d_bits, identity_map(h.n),
-                                st)) != RCS_OK ||
-            (rc = launch_xeb(h.psi, h.n, h.d_bits, h.shots, h.total, h.d_xeb + 1, h.d_xeb, identity_map(h.n), st)) !=
-                RCS_OK)
-            return bfail(b, rc, "sampling launch: " + take_launch_error());
-    }
+    for (size_t i = 0; i < b->inst.size(); ++i)
+        if ((rc = launch_sampling(b, b->inst[i], b->side[i % b->side.size()])) != RCS_OK) return rc;
     for (size_t j = 0; j < b->side.size(); ++j) {
         BCUDA(b, cudaEventRecord(b->ev[1 + j], b->side[j]), "join event");
         BCUDA(b, cudaStreamWaitEvent(s0, b->ev[1 + j], 0), "join");
@@ -515,8 +590,17 @@ int rcs_batch_create(const rcs_batch_item *items, size_t n_items, const rcs_opts
     try {
         b = new rcs_batch;
         cudaGetDevice(&b->dev);
-        int k_fixed = opts ? opts->k_max : 0;
-        const bool tune = !opts || opts->autotune != 0 || k_fixed == 0;
+        b->tc = opts && (opts->precision == RCS_PREC_BF16X3 || opts->precision == RCS_PREC_TF32X3);
+        if (opts && (opts->precision < RCS_PREC_FP32_PLAIN || opts->precision > RCS_PREC_TF32X3)) {
+            free_batch(b);
+            return set_thread_error(RCS_ERR_ARG, "unknown precision");
+        }
+        int k_fixed = opts && !b->tc ? opts->k_max : 0;
+        const bool tune = !b->tc && (!opts || opts->autotune != 0 || k_fixed == 0);
+        if (b->tc && opts->k_max != 0 && opts->k_max != kTcK) {
+            free_batch(b);
+            return set_thread_error(RCS_ERR_ARG, "the tensor-core batch uses k_max = 6 (or 0)");
+        }
         if (k_fixed != 0 && (k_fixed < 2 || k_fixed > kMaxK)) {
             free_batch(b);
             return set_thread_error(RCS_ERR_ARG, "batched k_max must be 2..5 (0 = autotune)");
@@ -564,6 +648,45 @@ int rcs_batch_create(const rcs_batch_item *items, size_t n_items, const rcs_opts
         }
         BCUDA(b, cudaMalloc(&b->d_err, 8), "error word");
         BCUDA(b, cudaMemset(b->d_err, 0, 8), "error word");
+        if (b->tc) {
+            rcs_opts o{};
+            o.precision = opts->precision;
+            for (size_t i = 0; i < n_items; ++i) {
+                InstHost &h = b->inst[i];
+                std::vector<uint8_t> img;
+                int rc = plan_fresh_circuit(h.n, hg[i], o, &h.plan, &img);
+                if (rc != RCS_OK) {
+                    std::string m = "circuit " + std::to_string(i) + ": " + rcs_last_error(nullptr);
+                    free_batch(b);
+                    return set_thread_error(rc, m);
+                }
+                h.k = h.plan.k_max;
+                if (!img.empty()) {
+                    BCUDA(b, cudaMalloc(&h.d_ops, img.size()), "operand images");
+                    BCUDA(b, cudaMemcpy(h.d_ops, img.data(), img.size(), cudaMemcpyHostToDevice), "operand images");
+                }
+                h.prefix = plan_prefix(h.plan, &h.tmask);
+                if (h.prefix > 0) BCUDA(b, cudaMalloc(&h.d_sub, size_t(8) << std::popcount(h.tmask)), "sub-state");
+            }
+            if (int rc = tc_prepare_device(); rc != RCS_OK) {
+                std::string m = take_launch_error();
+                free_batch(b);
+                return set_thread_error(rc, m);
+            }
+            BCUDA(b, cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "stream");
+            const size_t nside = std::min<size_t>(32, n_items);
+            b->side.resize(nside, nullptr);
+            for (auto &s : b->side) BCUDA(b, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "stream");
+            b->ev.resize(1 + nside, nullptr);
+            for (auto &e : b->ev) BCUDA(b, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+            if (int rc = capture(b); rc != RCS_OK) {
+                std::string m = b->err;
+                free_batch(b);
+                return set_thread_error(rc, m);
+            }
+            *out = b;
+            return RCS_OK;
+        }
         // fusion width per circuit: fixed, or by timed trials on a scratch state of the largest size
         float2 *scratch = nullptr;
         if (tune) {
@@ -672,14 +795,34 @@ int rcs_batch_result(rcs_batch *b, size_t i, uint64_t *out_bits, double *out_xeb
 
 int rcs_batch_state_read(rcs_batch *b, size_t i, uint64_t first, uint64_t count, float *out_re_im) {
     if (!b || i >= b->inst.size()) return set_thread_error(RCS_ERR_ARG, "bad batch index");
-    const uint64_t lim = uint64_t(1) << b->inst[i].n;
+    const InstHost &h = b->inst[i];
+    const uint64_t lim = uint64_t(1) << h.n;
     if (first > lim || count > lim - first || (count && !out_re_im)) return set_thread_error(RCS_ERR_ARG, "bad range");
-    if (count) BCUDA(b, cudaMemcpy(out_re_im, b->inst[i].psi + first, count * 8, cudaMemcpyDeviceToHost), "read state");
+    if (!count) return RCS_OK;
+    if (h.plan.phys_of.empty()) {
+        BCUDA(b, cudaMemcpy(out_re_im, h.psi + first, count * 8, cudaMemcpyDeviceToHost), "read state");
+        return RCS_OK;
+    }
+    // stored in the plan's qubit layout: read it all and put caller index c at position c
+    try {
+        std::vector<float2> all(static_cast<size_t>(lim));
+        BCUDA(b, cudaMemcpy(all.data(), h.psi, lim * 8, cudaMemcpyDeviceToHost), "read state");
+        const BitMap m = plan_to_stored(h.plan);
+        float2 *out = reinterpret_cast<float2 *>(out_re_im);
+        for (uint64_t c = first; c < first + count; ++c) {
+            uint64_t s = 0;
+            for (int q = 0; q < h.n; ++q) s |= ((c >> q) & 1ull) << m.to[q];
+            out[c - first] = all[size_t(s)];
+        }
+    } catch (const std::bad_alloc &) {
+        return set_thread_error(RCS_ERR_OOM, "host allocation failed");
+    }
     return RCS_OK;
 }
 
 int rcs_batch_set_fault(rcs_batch *b, int64_t skip_item, double wait_limit_s) {
     if (!b) return set_thread_error(RCS_ERR_ARG, "null batch");
+    if (b->tc) return bfail(b, RCS_ERR_UNSUPPORTED, "the tensor-core batch has no work items to fault");
     int clk_khz = 0;
     cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, b->dev);
     b->skip_item = skip_item;

@@ -109,6 +109,9 @@ int launch_expand(void *psi, int n, const void *sub, uint64_t tmask, void *strea
 int plan_prefix(const Plan &plan, uint64_t *tmask);
 int launch_pass_plain(void *psi, int n, const Pass &p, void *stream);
 int launch_pass_simt(void *psi, int n, const Pass &p, void *stream);
+// Sets the tensor-core kernels' shared-memory attribute on the current device (once);
+// launch_pass_tc calls it, and a caller about to capture a graph calls it first.
+int tc_prepare_device();
 // tf32: the TF32x3 kernel (operand image from tc_build_ops(p, img, true)), else BF16x3.
 int launch_pass_tc(void *psi, int n, const Pass &p, const void *d_ops, int *d_err, void *stream, bool tf32);
 
@@ -118,18 +121,31 @@ size_t tc_ops_bytes(bool tf32);
 void tc_build_ops(const Pass &p, void *host_image, bool tf32);
 
 // Sampler / readout (k_sample.cu)
-int launch_block_sums(const void *psi, int n, uint64_t *bsum, int *d_err, void *stream);
+// to_stored: caller basis index -> stored index (the state's qubit layout). Blocks are
+// 1024 consecutive caller indices in every layout.
+int launch_block_sums(const void *psi, int n, uint64_t *bsum, int *d_err, const BitMap &to_stored, void *stream);
 size_t scan_chunks(int n);
 int launch_block_scan(const uint64_t *bsum, uint64_t *bpre, uint64_t *chunk_tot, uint64_t *total, int n, int *d_err,
                       void *stream);
-// out_map takes the drawn (stored) index to the caller's basis index; in_map takes
-// the caller's index to the stored one.
+// to_stored / in_map take the caller's basis index to the stored one. The sampler
+// draws the caller index x = min{i : C_i > u T} with C in the caller's order, from
+// block sums made with the same map.
 int launch_sample(const void *psi, int n, const uint64_t *bsum, const uint64_t *bpre, const uint64_t *total,
-                  uint64_t shots, uint64_t seed, uint64_t *d_out, const BitMap &out_map, void *stream);
+                  uint64_t shots, uint64_t seed, uint64_t *d_out, const BitMap &to_stored, void *stream);
 int launch_gather(const void *psi, int n, const uint64_t *d_bits, size_t count, double *d_out_re_im, int *d_err,
                   const BitMap &in_map, void *stream);
 int launch_xeb(const void *psi, int n, const uint64_t *d_samples, size_t count, const uint64_t *total,
                double *d_partials, double *d_out, const BitMap &in_map, void *stream);
 size_t xeb_partials_count(size_t count);
+
+// ---- planning shared by single circuits and batches (api.cu)
+// Plans a circuit for a fresh n-qubit state with the given options (a qubit layout
+// allowed) and builds the operand images of its tensor-core passes; thread error on failure.
+int plan_fresh_circuit(int n, const std::vector<HostGate> &gates, const rcs_opts &o, Plan *plan,
+                       std::vector<uint8_t> *images);
+// A pass of the plan's sub-state prefix, its targets renumbered into the sub-state of mask T.
+Pass substate_pass(const Pass &p, uint64_t T);
+// Bit map of a plan's layout: caller basis index -> stored index.
+BitMap plan_to_stored(const Plan &plan);
 
 }  // namespace rcs

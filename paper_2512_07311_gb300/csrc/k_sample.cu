@@ -13,12 +13,23 @@
 // Sampling (inverse CDF): x_s = smallest i with C_i > u_s * T. The comparison
 // C_i * 2^53 > m_s * T, with u_s = m_s * 2^-53, is done exactly in 128-bit integers.
 //   1. k_block_sums: S_b = sum of q over block b (1024 amplitudes), one warp per block.
+//
+// Blocks, prefixes and the walk follow the caller's basis order also when the state is
+// stored in a permuted qubit layout (caller bit q at stored bit to[q]): then block b is
+// the 1024 caller indices [1024 b, 1024 b + 1024), whose stored positions vary in the
+// bits P = {to[0..9]}. k_block_sums_map reads tiles that vary in the stored bits
+// P u {0..4} (coalesced, lane = stored bits 0..4); each lane's amplitudes then lie in
+// one caller block, and lanes of the same block are combined by shuffles. k_sample
+// gathers the chosen block in caller order. So x_s is the same index, for the same
+// uniform, whatever the layout.
 //   2. k_scan_*:     exclusive prefix P_b of S_b, and T = sum_b S_b.
 //   3. k_sample:     one warp per shot: Philox4x64-10 uniform, binary search of the
 //                    block with P_b + S_b crossing the target, warp prefix over the
 //                    block's 32-amplitude lane ranges, sequential walk in one lane.
 // XEB: k_xeb_partial / k_xeb_final gather |psi_x|^2 in FP64 and reduce in a fixed
 // tree order, F = 2^n * mean / T - 1.
+#include <bit>
+
 #include "dev_common.cuh"
 #include "internal.h"
 
@@ -65,12 +76,55 @@ __global__ void __launch_bounds__(256) k_block_sums(const float2 *__restrict__ p
     if (bad) atomicOr(d_err, 1);
 }
 
-int launch_block_sums(const void *psi, int n, uint64_t *bsum, int *d_err, void *stream) {
+// Layout form: tile t = all amplitudes whose stored bits outside `tsmask` equal t's
+// bits (deposited in order). `inner` = tsmask minus bits 0..4 (walked by the loop),
+// `plane` = the lane bits that lie in P (lanes differing only there share a block).
+__global__ void __launch_bounds__(256) k_block_sums_map(const float2 *__restrict__ psi, int n, uint64_t tsmask,
+                                                         uint64_t inner, uint32_t plane, uint64_t ntiles, int blog2,
+                                                         const BitMap to_caller, uint64_t *__restrict__ bsum,
+                                                         int *__restrict__ d_err) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
+    int bad = 0;
+    for (uint64_t t = uint64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); t < ntiles; t += warps) {
+        uint64_t base = 0;
+        for (int bit = 0, k = 0; bit < n; ++bit)
+            if (!((tsmask >> bit) & 1ull)) base |= ((t >> k++) & 1ull) << bit;
+        base |= uint64_t(lane);
+        uint64_t s = 0, off = 0;
+        do {  // every value of the inner bits, in increasing order (masked increment)
+            s += fx_amp(__ldg(psi + (base | off)), bad);
+            off = ((off | ~inner) + 1ull) & inner;
+        } while (off != 0);
+#pragma unroll
+        for (int bit = 0; bit < 5; ++bit)
+            if ((plane >> bit) & 1u) s += __shfl_xor_sync(0xffffffffu, s, 1 << bit);
+        if ((uint32_t(lane) & plane) == 0) bsum[map_bits(to_caller, base) >> blog2] = s;
+    }
+    if (bad) atomicOr(d_err, 1);
+}
+
+int launch_block_sums(const void *psi, int n, uint64_t *bsum, int *d_err, const BitMap &to_stored, void *stream) {
     const int bl = block_log2(n);
     const uint64_t nblocks = 1ull << (n - bl);
-    const unsigned grid = grid_for(nblocks * 32, 256, device_sm_count(), 8);
-    k_block_sums<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<const float2 *>(psi), bl, nblocks,
-                                                                      bsum, d_err);
+    if (to_stored.identity) {
+        const unsigned grid = grid_for(nblocks * 32, 256, device_sm_count(), 8);
+        k_block_sums<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<const float2 *>(psi), bl,
+                                                                          nblocks, bsum, d_err);
+        return launch_status(__func__);
+    }
+    // the tile bits P u {0..4} lie below n (layouts are only chosen for n >= 12)
+    uint64_t pmask = 0;
+    for (int q = 0; q < bl; ++q) pmask |= 1ull << to_stored.to[q];
+    const uint64_t tsmask = pmask | 31ull;
+    const uint64_t ntiles = 1ull << (n - std::popcount(tsmask));
+    BitMap to_caller = identity_map(n);
+    to_caller.identity = 0;
+    for (int q = 0; q < n; ++q) to_caller.to[to_stored.to[q]] = uint8_t(q);
+    const unsigned grid = grid_for(ntiles * 32, 256, device_sm_count(), 8);
+    k_block_sums_map<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const float2 *>(psi), n, tsmask, tsmask & ~31ull, uint32_t(pmask & 31ull), ntiles, bl, to_caller,
+        bsum, d_err);
     return launch_status(__func__);
 }
 
@@ -207,16 +261,31 @@ __device__ __forceinline__ bool above(uint64_t a, uint64_t rhi, uint64_t rlo) {
 
 // ---------------------------------------------------------------- sampler
 
+// smap: caller index -> stored index (identity: the plain contiguous block reads).
 __global__ void __launch_bounds__(256) k_sample(const float2 *__restrict__ psi, int blog2, uint64_t nblocks,
                                                  const uint64_t *__restrict__ bsum,
                                                  const uint64_t *__restrict__ bpre,
                                                  const uint64_t *__restrict__ total, uint64_t shots, uint64_t seed,
-                                                 uint64_t *__restrict__ out, const BitMap out_map) {
+                                                 uint64_t *__restrict__ out, const BitMap smap) {
     const int lane = threadIdx.x & 31;
     const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
     const uint64_t T = *total;
     const uint32_t bamps = 1u << blog2;
     int bad = 0;
+    // layout: stored offset of caller offset 32 lane + a = lmap | emap[a] (disjoint bits)
+    __shared__ uint64_t emap[32];
+    uint64_t lmap = 0;
+    if (!smap.identity) {
+        if (threadIdx.x < 32) {
+            uint64_t e = 0;
+            for (int q = 0; q < 5; ++q)
+                if ((threadIdx.x >> q) & 1) e |= 1ull << smap.to[q];
+            emap[threadIdx.x] = e;
+        }
+        for (int q = 5; q < blog2; ++q)
+            if (((32u * uint32_t(lane)) >> q) & 1u) lmap |= 1ull << smap.to[q];
+        __syncthreads();
+    }
     for (uint64_t s = uint64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); s < shots; s += warps) {
         if (T == 0) {
             if (lane == 0) out[s] = ~0ull;
@@ -233,8 +302,32 @@ __global__ void __launch_bounds__(256) k_sample(const float2 *__restrict__ psi, 
         }
         const uint64_t b = lo;
         const uint64_t base = bpre[b];
-        const float2 *blk = psi + (b << blog2);
         const uint32_t a0 = uint32_t(lane) * 32u;
+        if (!smap.identity) {  // blog2 = 10: every lane owns 32 caller offsets
+            const float2 *lb = psi + (map_bits(smap, b << blog2) | lmap);
+            uint64_t ls = 0;
+#pragma unroll 8
+            for (int a = 0; a < 32; ++a) ls += fx_amp(__ldg(lb + emap[a]), bad);
+            const uint64_t incl = warp_incl_scan_u64(ls, lane);
+            const unsigned hit = __ballot_sync(0xffffffffu, above(base + incl, rhi, rlo));
+            const int L = __ffs(hit) - 1;
+            uint64_t idx = 0;
+            if (lane == L) {
+                uint64_t run = base + incl - ls;
+                idx = (b << blog2) + a0 + 31;
+                for (int a = 0; a < 32; ++a) {
+                    run += fx_amp(lb[emap[a]], bad);
+                    if (above(run, rhi, rlo)) {
+                        idx = (b << blog2) + a0 + uint32_t(a);
+                        break;
+                    }
+                }
+            }
+            idx = __shfl_sync(0xffffffffu, idx, L < 0 ? 0 : L);
+            if (lane == 0) out[s] = idx;
+            continue;
+        }
+        const float2 *blk = psi + (b << blog2);
         uint64_t ls = 0;
         if (a0 < bamps) {
             const uint32_t cnt = bamps - a0 < 32u ? bamps - a0 : 32u;
@@ -260,7 +353,7 @@ __global__ void __launch_bounds__(256) k_sample(const float2 *__restrict__ psi, 
             }
         }
         idx = __shfl_sync(0xffffffffu, idx, L < 0 ? 0 : L);
-        if (lane == 0) out[s] = map_bits(out_map, idx);
+        if (lane == 0) out[s] = idx;
     }
 }
 
@@ -273,13 +366,14 @@ BitMap identity_map(int n) {
 }
 
 int launch_sample(const void *psi, int n, const uint64_t *bsum, const uint64_t *bpre, const uint64_t *total,
-                  uint64_t shots, uint64_t seed, uint64_t *d_out, const BitMap &out_map, void *stream) {
+                  uint64_t shots, uint64_t seed, uint64_t *d_out, const BitMap &to_stored, void *stream) {
     if (shots == 0) return RCS_OK;
     const int bl = block_log2(n);
+    if (!to_stored.identity && bl < 10) return RCS_ERR_UNSUPPORTED;
     const uint64_t nblocks = 1ull << (n - bl);
     const unsigned grid = grid_for(shots * 32, 256, device_sm_count(), 8);
     k_sample<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<const float2 *>(psi), bl, nblocks, bsum,
-                                                                  bpre, total, shots, seed, d_out, out_map);
+                                                                  bpre, total, shots, seed, d_out, to_stored);
     return launch_status(__func__);
 }
 

@@ -778,20 +778,23 @@ static int set_smem_attr() {
     return e == cudaSuccess ? RCS_OK : note_launch_error("tensor-core kernel shared-memory attribute", e);
 }
 
-int launch_pass_tc(void *psi, int n, const Pass &p, const void *d_ops, int *d_err, void *stream, bool tf32) {
-    using namespace tc;
-    if (p.k != K || n < K + 7) return RCS_ERR_UNSUPPORTED;
+int tc_prepare_device() {
     static bool attr_done[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev < 64 && !attr_done[dev]) {
-        int rc = set_smem_attr<false, false>();
-        if (rc == RCS_OK) rc = set_smem_attr<true, false>();
-        if (rc == RCS_OK) rc = set_smem_attr<false, true>();
-        if (rc == RCS_OK) rc = set_smem_attr<true, true>();
-        if (rc != RCS_OK) return rc;
-        attr_done[dev] = true;
-    }
+    if (dev >= 0 && dev < 64 && attr_done[dev]) return RCS_OK;
+    int rc = set_smem_attr<false, false>();
+    if (rc == RCS_OK) rc = set_smem_attr<true, false>();
+    if (rc == RCS_OK) rc = set_smem_attr<false, true>();
+    if (rc == RCS_OK) rc = set_smem_attr<true, true>();
+    if (rc == RCS_OK && dev >= 0 && dev < 64) attr_done[dev] = true;
+    return rc;
+}
+
+int launch_pass_tc(void *psi, int n, const Pass &p, const void *d_ops, int *d_err, void *stream, bool tf32) {
+    using namespace tc;
+    if (p.k != K || n < K + 7) return RCS_ERR_UNSUPPORTED;
+    if (int rc = tc_prepare_device(); rc != RCS_OK) return rc;
     TcArgs a;
     a.psi = static_cast<float2 *>(psi);
     a.ops = static_cast<const uint4 *>(d_ops);

@@ -139,3 +139,63 @@ def test_batched_workload_64(lib, oracle):
         assert checked >= 3
     finally:
         capi.rcs_batch_destroy(b)
+
+
+# ------------------------------------------------------------------ tensor-core engine
+
+@pytest.mark.parametrize("precision", [capi.RCS_PREC_BF16X3, capi.RCS_PREC_TF32X3])
+def test_batch_tensor_core_vs_oracle(lib, oracle, precision):
+    """The tensor-core engine: each circuit planned with its own layout and sub-state
+    prefix (12 qubits: the FP32 fallback), states, samples and XEB in the circuit's own
+    qubit numbering."""
+    circs = small_batch()
+    shots = 20_000
+    b = capi.rcs_batch_create([(c.n_qubits, c.gates, shots, 40 + i) for i, c in enumerate(circs)],
+                              precision=precision)
+    try:
+        for _ in range(2):  # the graph replays
+            capi.rcs_batch_launch(b)
+            capi.rcs_batch_wait(b)
+        for i, c in enumerate(circs):
+            info = capi.rcs_batch_info(b, i)
+            assert info["k"] == (6 if c.n_qubits >= 13 else 5)
+            want = oracle.simulate(c.n_qubits, c.gates)
+            got = capi.rcs_batch_state_read(b, i)
+            assert infidelity(got, want) <= 1e-5
+            assert np.abs(got - want).max() <= 1e-6
+            xs, F = capi.rcs_batch_result(b, i, shots)
+            g128 = got.astype(np.complex128)
+            assert np.mean(xs == oracle.sample(g128, shots, 40 + i)) >= 0.9999
+            assert abs(F - oracle.xeb(g128, xs)) <= 1e-9
+        with pytest.raises(capi.RcsError) as e:
+            capi.rcs_batch_set_fault(b, 0, 0.1)
+        assert e.value.code == capi.RCS_ERR_UNSUPPORTED
+    finally:
+        capi.rcs_batch_destroy(b)
+
+
+def test_batched_workload_64_tensor_core(lib, oracle):
+    circs = C.batch_workload(64, 1000)
+    shots = 100_000
+    b = capi.rcs_batch_create([(c.n_qubits, c.gates, shots, c.seed) for c in circs], precision=capi.RCS_PREC_BF16X3)
+    try:
+        capi.rcs_batch_launch(b)
+        capi.rcs_batch_wait(b)
+        checked = 0
+        for i, c in enumerate(circs):
+            got = capi.rcs_batch_state_read(b, i).astype(np.complex128)
+            p = np.abs(got) ** 2
+            T = p.sum()
+            assert abs(T - 1) <= 2e-6 * capi.rcs_batch_info(b, i)["n_passes"]
+            xs, F = capi.rcs_batch_result(b, i, shots)
+            assert (p[xs.astype(np.int64)] > 0).all()
+            q = p / T
+            mean = (1 << c.n_qubits) * float(np.sum(q * q)) - 1
+            sd = (1 << c.n_qubits) * math.sqrt(max(float(np.sum(q ** 3)) - float(np.sum(q * q)) ** 2, 0)) / math.sqrt(shots)
+            assert abs(F - mean) <= 6 * sd + 1e-9, (i, F, mean, sd)
+            if c.n_qubits <= 20 and checked < 6:
+                assert infidelity(got, oracle.simulate(c.n_qubits, c.gates)) <= 1e-5
+                checked += 1
+        assert checked >= 3
+    finally:
+        capi.rcs_batch_destroy(b)

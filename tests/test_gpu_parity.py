@@ -378,3 +378,28 @@ def test_device_pointer_calls(lib, oracle):
         assert math.isnan(float(d_xeb.item()))
     finally:
         capi.rcs_destroy(ctx)
+
+
+@pytest.mark.parametrize("n,precision", [(20, capi.RCS_PREC_BF16X3), (24, capi.RCS_PREC_FP32_FUSED)])
+def test_sampler_follows_caller_order_in_any_layout(lib, oracle, n, precision):
+    """With the state stored in a permuted qubit layout, the sampler still draws
+    x = min{i : C_i > u T} with C in the circuit's own index order: the same shots as
+    the oracle sampler on the same state, drawn before anything restores the layout."""
+    circ = C.generate(C.grid_for_n(n), cycles=8, pattern="EFGH", seed=123)
+    ctx = capi.rcs_create(circ.grid, precision)
+    try:
+        capi.rcs_apply_circuit(ctx, circ.gates)
+        phys = capi.rcs_qubit_layout(ctx)
+        assert any(int(p) != q for q, p in enumerate(phys)), "the test needs a non-identity layout"
+        shots, seed = 100_000, 77
+        xs = capi.rcs_sample(ctx, shots, seed)
+        norm = capi.rcs_norm(ctx)
+        F = capi.rcs_xeb(ctx, xs)
+        got = capi.rcs_state_read(ctx).astype(np.complex128)  # restores the identity layout
+        assert abs(np.vdot(got, got).real - norm) <= 1e-9
+        xo = oracle.sample(got, shots, seed)
+        assert np.mean(xs == xo) >= 0.9999
+        assert abs(F - oracle.xeb(got, xs)) <= 1e-9
+        assert np.array_equal(capi.rcs_sample(ctx, shots, seed), xs)  # identity layout now: same draws
+    finally:
+        capi.rcs_destroy(ctx)
