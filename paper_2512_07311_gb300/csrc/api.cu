@@ -199,13 +199,21 @@ int build_plan(rcs_ctx *ctx, int n, const std::vector<HostGate> &hg, const rcs_o
     plan->precision = o.precision;
     plan->n_gates = int64_t(hg.size());
     plan->phys_of.clear();
+    plan->prefix_span = 0;
+    // allow_layout: the plan is for a fresh state, so it may choose a layout and is
+    // planned for a run from |0...0> (sub-state prefix counted)
     auto fused = [&](int k, int pad) {
-        const Blocking bl = plan_blocks(n, hg, k);
+        Blocking bl = plan_blocks(n, hg, k, allow_layout);
+        plan->prefix_span = bl.span;
         int phys[64];
         if (allow_layout && choose_layout(n, hg, bl, phys)) {
             std::vector<HostGate> moved = hg;
             for (HostGate &g : moved)
                 for (int a = 0; a < g.nq; ++a) g.q[a] = phys[g.q[a]];
+            uint64_t avoid = 0;
+            for (int q = 0; q < n; ++q)
+                if ((bl.avoid >> q) & 1) avoid |= 1ull << phys[q];
+            bl.avoid = avoid;
             make_passes(n, moved, bl, pad, &plan->passes);
             plan->phys_of.assign(phys, phys + n);
         } else {

@@ -55,6 +55,7 @@ struct Plan {
     int k_max = 4;
     int64_t n_gates = 0;
     std::vector<Pass> passes;
+    int prefix_span = 0;  // widest sub-state of a run from |0...0> (0: n - 4)
     // device copies, per context device (uploaded lazily)
     int dev = -1;
     void *d_tc_ops = nullptr;   // hi/lo operand images of PASS_TC passes
@@ -69,8 +70,12 @@ void plan_fuse(int n, const std::vector<HostGate> &gates, int k_max, int pad_to,
 // how the qubits are labelled), then the passes for a gate list with those blocks.
 struct Blocking {
     std::vector<std::vector<int>> gates;  // gate indices of each block, in application order
+    int span = 0;        // run from |0...0>: leading blocks within `span` qubits use a sub-state
+    uint64_t avoid = 0;  // qubits that padding keeps out of blocks (those outside the sub-state)
 };
-Blocking plan_blocks(int n, const std::vector<HostGate> &gates, int k_max);
+// from_zero: the blocks will run from |0...0>, so they are chosen by cost with the
+// sub-state prefix counted (see planner.cpp); otherwise by fewest blocks.
+Blocking plan_blocks(int n, const std::vector<HostGate> &gates, int k_max, bool from_zero);
 void make_passes(int n, const std::vector<HostGate> &gates, const Blocking &b, int pad_to, std::vector<Pass> *out);
 
 // Physical position of every logical qubit for a blocking (phys_of[logical]): up

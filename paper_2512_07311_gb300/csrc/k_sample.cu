@@ -18,8 +18,9 @@
 // stored in a permuted qubit layout (caller bit q at stored bit to[q]): then block b is
 // the 1024 caller indices [1024 b, 1024 b + 1024), whose stored positions vary in the
 // bits P = {to[0..9]}. k_block_sums_map reads tiles that vary in the stored bits
-// P u {0..4} (coalesced, lane = stored bits 0..4); each lane's amplitudes then lie in
-// one caller block, and lanes of the same block are combined by shuffles. k_sample
+// P u {0..5} (coalesced: lane = stored bits 1..5, a float4 = stored bit 0); each
+// lane's amplitudes then lie in one or two caller blocks, and lanes of the same block
+// are combined by shuffles. k_sample
 // gathers the chosen block in caller order. So x_s is the same index, for the same
 // uniform, whatever the layout.
 //   2. k_scan_*:     exclusive prefix P_b of S_b, and T = sum_b S_b.
@@ -76,13 +77,16 @@ __global__ void __launch_bounds__(256) k_block_sums(const float2 *__restrict__ p
     if (bad) atomicOr(d_err, 1);
 }
 
-// Layout form: tile t = all amplitudes whose stored bits outside `tsmask` equal t's
-// bits (deposited in order). `inner` = tsmask minus bits 0..4 (walked by the loop),
-// `plane` = the lane bits that lie in P (lanes differing only there share a block).
+// Layout form: tile t = all amplitudes whose stored bits outside `tsmask` = P u {0..5}
+// equal t's bits (deposited in order). Lane = stored bits 1..5 and a float4 carries the
+// two amplitudes of stored bit 0, so a load instruction reads 512 contiguous bytes;
+// `inner` = tsmask minus bits 0..5 is walked by the loop. Every amplitude of a lane
+// with the same stored bit 0 lies in one caller block; `plane` = the lane bits in P
+// (lanes that differ only there share a block), `b0p` = stored bit 0 is in P.
 __global__ void __launch_bounds__(256) k_block_sums_map(const float2 *__restrict__ psi, int n, uint64_t tsmask,
-                                                         uint64_t inner, uint32_t plane, uint64_t ntiles, int blog2,
-                                                         const BitMap to_caller, uint64_t *__restrict__ bsum,
-                                                         int *__restrict__ d_err) {
+                                                         uint64_t inner, uint32_t plane, int b0p, uint64_t ntiles,
+                                                         int blog2, const BitMap to_caller,
+                                                         uint64_t *__restrict__ bsum, int *__restrict__ d_err) {
     const int lane = threadIdx.x & 31;
     const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
     int bad = 0;
@@ -90,16 +94,25 @@ __global__ void __launch_bounds__(256) k_block_sums_map(const float2 *__restrict
         uint64_t base = 0;
         for (int bit = 0, k = 0; bit < n; ++bit)
             if (!((tsmask >> bit) & 1ull)) base |= ((t >> k++) & 1ull) << bit;
-        base |= uint64_t(lane);
-        uint64_t s = 0, off = 0;
+        base |= uint64_t(lane) << 1;
+        uint64_t s0 = 0, s1 = 0, off = 0;
         do {  // every value of the inner bits, in increasing order (masked increment)
-            s += fx_amp(__ldg(psi + (base | off)), bad);
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(psi + (base | off)));
+            s0 += fx_sq(v.x, bad) + fx_sq(v.y, bad);
+            s1 += fx_sq(v.z, bad) + fx_sq(v.w, bad);
             off = ((off | ~inner) + 1ull) & inner;
         } while (off != 0);
+        if (b0p) s0 += s1;
 #pragma unroll
         for (int bit = 0; bit < 5; ++bit)
-            if ((plane >> bit) & 1u) s += __shfl_xor_sync(0xffffffffu, s, 1 << bit);
-        if ((uint32_t(lane) & plane) == 0) bsum[map_bits(to_caller, base) >> blog2] = s;
+            if ((plane >> bit) & 1u) {
+                s0 += __shfl_xor_sync(0xffffffffu, s0, 1 << bit);
+                s1 += __shfl_xor_sync(0xffffffffu, s1, 1 << bit);
+            }
+        if ((uint32_t(lane) & plane) == 0) {
+            bsum[map_bits(to_caller, base) >> blog2] = s0;
+            if (!b0p) bsum[map_bits(to_caller, base | 1ull) >> blog2] = s1;
+        }
     }
     if (bad) atomicOr(d_err, 1);
 }
@@ -113,18 +126,18 @@ int launch_block_sums(const void *psi, int n, uint64_t *bsum, int *d_err, const 
                                                                           nblocks, bsum, d_err);
         return launch_status(__func__);
     }
-    // the tile bits P u {0..4} lie below n (layouts are only chosen for n >= 12)
+    // the tile bits P u {0..5} lie below n (layouts are only chosen for n >= 12)
     uint64_t pmask = 0;
     for (int q = 0; q < bl; ++q) pmask |= 1ull << to_stored.to[q];
-    const uint64_t tsmask = pmask | 31ull;
+    const uint64_t tsmask = pmask | 63ull;
     const uint64_t ntiles = 1ull << (n - std::popcount(tsmask));
     BitMap to_caller = identity_map(n);
     to_caller.identity = 0;
     for (int q = 0; q < n; ++q) to_caller.to[to_stored.to[q]] = uint8_t(q);
     const unsigned grid = grid_for(ntiles * 32, 256, device_sm_count(), 8);
     k_block_sums_map<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        static_cast<const float2 *>(psi), n, tsmask, tsmask & ~31ull, uint32_t(pmask & 31ull), ntiles, bl, to_caller,
-        bsum, d_err);
+        static_cast<const float2 *>(psi), n, tsmask, tsmask & ~63ull, uint32_t((pmask >> 1) & 31ull), int(pmask & 1ull),
+        ntiles, bl, to_caller, bsum, d_err);
     return launch_status(__func__);
 }
 

@@ -10,7 +10,10 @@
 // order equals the circuit.
 #include <algorithm>
 #include <bit>
+#include <cmath>
 #include <cstring>
+#include <map>
+#include <thread>
 
 #include "internal.h"
 
@@ -105,7 +108,7 @@ struct Block {
 // ties go to the gate after which most of the next `window` gates on its new qubits
 // would fit in the block (window > 0), then to the earliest gate. A seed >= 0 is
 // taken first.
-Block grow(const Dag &d, std::vector<size_t> &head, int k_max, int window, int seed) {
+Block grow(const Dag &d, std::vector<size_t> &head, int k_max, int window, int seed, uint64_t allow = ~0ull) {
     Block b;
     std::vector<int> ready;
     if (seed >= 0) {
@@ -117,6 +120,7 @@ Block grow(const Dag &d, std::vector<size_t> &head, int k_max, int window, int s
         d.ready_gates(head, &ready);
         int best = -1, best_new = 1 << 30, best_aff = -1;
         for (int gi : ready) {
+            if (d.mask[gi] & ~allow) continue;
             const uint64_t nm = b.Q | d.mask[gi];
             if (std::popcount(nm) > k_max) continue;
             const int nnew = std::popcount(d.mask[gi] & ~b.Q);
@@ -147,29 +151,34 @@ Block grow(const Dag &d, std::vector<size_t> &head, int k_max, int window, int s
 }
 
 // One complete blocking of the circuit. seed_search: start every block from the ready
-// gate whose grown block holds the most gates (earliest seed on ties).
-std::vector<Block> blocking(const Dag &d, size_t G, int k_max, int window, bool seed_search) {
+// gate whose grown block holds the most gates (earliest seed on ties). With `allow`
+// (a qubit mask) only gates inside it are placed, and the blocking ends when none is
+// ready; `head`/`placed` give the start and receive the end.
+std::vector<Block> blocking_from(const Dag &d, size_t G, int k_max, int window, bool seed_search, uint64_t allow,
+                                 std::vector<size_t> &head, size_t &placed) {
     std::vector<Block> blocks;
-    std::vector<size_t> head(d.n, 0);
-    size_t placed = 0;
     std::vector<int> seeds;
     while (placed < G) {
         if (!seed_search) {
-            blocks.push_back(grow(d, head, k_max, window, -1));
+            Block b = grow(d, head, k_max, window, -1, allow);
+            if (b.gates.empty()) break;
+            blocks.push_back(std::move(b));
         } else {
             d.ready_gates(head, &seeds);
             Block best;
             std::vector<size_t> best_head;
             int best_first = 1 << 30;
             for (int sd : seeds) {
+                if (d.mask[sd] & ~allow) continue;
                 std::vector<size_t> h = head;
-                Block b = grow(d, h, k_max, window, sd);
+                Block b = grow(d, h, k_max, window, sd, allow);
                 if (b.gates.size() > best.gates.size() || (b.gates.size() == best.gates.size() && sd < best_first)) {
                     best = std::move(b);
                     best_head = std::move(h);
                     best_first = sd;
                 }
             }
+            if (best.gates.empty()) break;
             head = std::move(best_head);
             blocks.push_back(std::move(best));
         }
@@ -178,13 +187,162 @@ std::vector<Block> blocking(const Dag &d, size_t G, int k_max, int window, bool 
     return blocks;
 }
 
+std::vector<Block> blocking(const Dag &d, size_t G, int k_max, int window, bool seed_search) {
+    std::vector<size_t> head(size_t(d.n), 0);
+    size_t placed = 0;
+    return blocking_from(d, G, k_max, window, seed_search, ~0ull, head, placed);
+}
+
+// Beam search over blockings. A state is the frontier (queue heads) after some blocks;
+// the number of gates placed follows from it. Each step grows, from every state, the
+// block seeded by each ready gate (the same growth rule as above), keeps the
+// `expand` largest per state, merges equal frontiers, and keeps the `width` states
+// with the most gates placed. The first state to place every gate ends the search;
+// its blocks are read back through the parent links. The expansions of a step run on
+// host threads, each state writing its own slot, and the merge walks the slots in
+// order, so the result does not depend on thread timing.
+std::vector<Block> beam_blocking(const Dag &d, size_t G, int k_max, int window, int width, int expand,
+                                 const std::vector<size_t> &head0, size_t placed0) {
+    struct Node {
+        int parent;
+        std::vector<int> gates;  // the block that led here
+    };
+    struct State {
+        std::vector<size_t> head;
+        size_t placed;
+        int node;  // index into this step's nodes
+    };
+    struct Cand {
+        size_t placed;
+        int seed;
+        std::vector<size_t> head;
+        Block b;
+    };
+    std::vector<std::vector<Node>> steps;
+    std::vector<State> states{State{head0, placed0, -1}};
+    const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    while (true) {
+        for (const State &st : states)
+            if (st.placed == G) {
+                std::vector<Block> out(steps.size());
+                int node = st.node;
+                for (size_t k = steps.size(); k-- > 0;) {
+                    out[k].gates = steps[k][size_t(node)].gates;
+                    node = steps[k][size_t(node)].parent;
+                }
+                return out;
+            }
+        std::vector<std::vector<Cand>> slot(states.size());
+        auto work = [&](size_t i) {
+            std::vector<int> seeds;
+            d.ready_gates(states[i].head, &seeds);
+            std::vector<Cand> cs;
+            cs.reserve(seeds.size());
+            for (int sd : seeds) {
+                Cand c;
+                c.head = states[i].head;
+                c.b = grow(d, c.head, k_max, window, sd);
+                c.placed = states[i].placed + c.b.gates.size();
+                c.seed = sd;
+                cs.push_back(std::move(c));
+            }
+            std::stable_sort(cs.begin(), cs.end(), [](const Cand &x, const Cand &y) {
+                return x.placed != y.placed ? x.placed > y.placed : x.seed < y.seed;
+            });
+            if (cs.size() > size_t(expand)) cs.resize(size_t(expand));
+            slot[i] = std::move(cs);
+        };
+        const size_t nt = std::min<size_t>(hw, states.size());
+        if (nt <= 1) {
+            for (size_t i = 0; i < states.size(); ++i) work(i);
+        } else {
+            std::vector<std::thread> pool;
+            for (size_t t = 0; t < nt; ++t)
+                pool.emplace_back([&, t] {
+                    for (size_t i = t; i < states.size(); i += nt) work(i);
+                });
+            for (std::thread &th : pool) th.join();
+        }
+        // merge equal frontiers (first occurrence in state order wins ties), keep the best `width`
+        std::map<std::vector<size_t>, std::pair<size_t, size_t>> seen;  // head -> (slot, index)
+        std::vector<std::pair<size_t, size_t>> order;
+        for (size_t i = 0; i < slot.size(); ++i)
+            for (size_t j = 0; j < slot[i].size(); ++j) {
+                auto it = seen.find(slot[i][j].head);
+                if (it == seen.end()) {
+                    seen.emplace(slot[i][j].head, std::make_pair(i, j));
+                    order.emplace_back(i, j);
+                }
+            }
+        if (order.empty()) return {};
+        std::stable_sort(order.begin(), order.end(), [&](const auto &x, const auto &y) {
+            return slot[x.first][x.second].placed > slot[y.first][y.second].placed;
+        });
+        if (order.size() > size_t(width)) order.resize(size_t(width));
+        std::vector<Node> nodes;
+        std::vector<State> next;
+        for (const auto &o : order) {
+            Cand &c = slot[o.first][o.second];
+            nodes.push_back(Node{states[o.first].node, std::move(c.b.gates)});
+            next.push_back(State{std::move(c.head), c.placed, int(nodes.size() - 1)});
+        }
+        steps.push_back(std::move(nodes));
+        states = std::move(next);
+    }
+}
+
+}  // namespace
+
+constexpr int kBeamWidth = 32;  // states kept per step of the beam search
+constexpr int kBeamExpand = 8;  // blocks grown per state and step
+
+namespace {
+
+// Gates that can run before any gate touching a qubit outside W: one scan in circuit
+// order (a gate is in iff it lies in W and none of its qubits has met a gate that
+// is out). Returns their number.
+size_t closure_size(const std::vector<HostGate> &gates, int n, uint64_t W) {
+    uint64_t blocked = 0;
+    size_t in = 0;
+    for (const HostGate &g : gates) {
+        uint64_t m = 0;
+        for (int a = 0; a < g.nq; ++a) m |= 1ull << g.q[a];
+        if ((m & ~W) == 0 && (m & blocked) == 0) ++in;
+        else blocked |= m;
+    }
+    (void)n;
+    return in;
+}
+
+// Cost of a blocking run from |0...0>, in full-state passes: the leading blocks whose
+// qubits span at most `span` qubits run on a 2^span sub-state (2^(span-n) each).
+double zero_cost(const Dag &d, const std::vector<Block> &b, int n, int span) {
+    uint64_t U = 0;
+    size_t p = 0;
+    for (const Block &blk : b) {
+        uint64_t m = 0;
+        for (int gi : blk.gates) m |= d.mask[size_t(gi)];
+        if (std::popcount(U | m) > span) break;
+        U |= m;
+        ++p;
+    }
+    if (p < 2) p = 0;
+    return double(b.size() - p) + double(p) * std::ldexp(1.0, span - n);
+}
+
 }  // namespace
 
 // Fuses the gates into blocks of at most k_max qubits. Several greedy blockings are
-// built -- the plain frontier rule, and best-seed growth with affinity windows of
-// 0, 1, 2, 3 and 6 next gates -- and the one with the fewest blocks is kept (on the
-// 34-qubit 20-cycle workload at k = 6: 51 blocks for the plain rule, 45 kept).
-Blocking plan_blocks(int n, const std::vector<HostGate> &gates, int k_max) {
+// built -- the plain frontier rule, best-seed growth with affinity windows of 0, 1, 2,
+// 3 and 6 next gates, and a beam search -- and the one with the fewest blocks is kept.
+// For a run from |0...0> (from_zero) the choice is by cost instead, and a second kind
+// of candidate is added: for k = 2..5 excluded qubits (chosen greedily to keep the
+// largest closure, the gates that precede every gate on them), the closure is blocked
+// inside the other n - k qubits, where its passes run on a 2^(n-k) sub-state, and the
+// rest of the circuit is blocked after it (greedily to pick k, then by beam search).
+// On the 34-qubit 20-cycle workload at k = 6 this takes the full-state passes from
+// 37 (45 passes, 8 of them on a 30-qubit sub-state) to 27 (16 more on a 31-qubit one).
+Blocking plan_blocks(int n, const std::vector<HostGate> &gates, int k_max, bool from_zero) {
     const size_t G = gates.size();
     k_max = std::max(2, std::min(k_max, n));
     Dag d;
@@ -200,14 +358,84 @@ Blocking plan_blocks(int n, const std::vector<HostGate> &gates, int k_max) {
         }
         d.mask[g] = m;
     }
+    const int default_span = n - 4;
     std::vector<Block> best = blocking(d, G, k_max, 0, false);
     const std::pair<int, bool> variants[] = {{0, true}, {1, true}, {2, true}, {3, true}, {6, true}};
     for (const auto &v : variants) {
         if (G == 0) break;
         std::vector<Block> b = blocking(d, G, k_max, v.first, v.second);
-        if (b.size() < best.size()) best = std::move(b);
+        const bool better = from_zero ? zero_cost(d, b, n, default_span) < zero_cost(d, best, n, default_span)
+                                      : b.size() < best.size();
+        if (better) best = std::move(b);
     }
     Blocking out;
+    out.span = default_span;
+    if (!from_zero) {
+        for (int window : {0, 2}) {
+            if (G == 0) break;
+            std::vector<Block> b =
+                beam_blocking(d, G, k_max, window, kBeamWidth, kBeamExpand, std::vector<size_t>(size_t(d.n), 0), 0);
+            if (!b.empty() && b.size() < best.size()) best = std::move(b);
+        }
+    } else if (G > 0) {
+        const uint64_t full = n >= 64 ? ~0ull : ((1ull << n) - 1ull);
+        double best_cost = zero_cost(d, best, n, default_span);
+        struct Cand {
+            double est = 1e300;
+            int k = 0;
+            uint64_t X = 0;
+            std::vector<Block> pre;
+            std::vector<size_t> head;
+            size_t placed = 0;
+        } pick;
+        for (int k = 2; k <= 5; ++k) {
+            if (n - k < std::max(kTcK + 7, k_max)) break;
+            uint64_t X = 0;
+            for (int r = 0; r < k; ++r) {  // exclude the qubit that keeps the closure largest
+                size_t bsize = 0;
+                int bq = -1;
+                for (int q = 0; q < n; ++q) {
+                    if ((X >> q) & 1) continue;
+                    const size_t c = closure_size(gates, n, full & ~(X | (1ull << q)));
+                    if (bq < 0 || c > bsize) {
+                        bsize = c;
+                        bq = q;
+                    }
+                }
+                X |= 1ull << bq;
+            }
+            Cand c;
+            c.k = k;
+            c.X = X;
+            c.head.assign(size_t(n), 0);
+            c.pre = blocking_from(d, G, k_max, 2, true, full & ~X, c.head, c.placed);
+            std::vector<size_t> h = c.head;
+            size_t pl = c.placed;
+            const std::vector<Block> rest = blocking_from(d, G, k_max, 2, true, ~0ull, h, pl);
+            c.est = double(rest.size()) + double(c.pre.size()) * std::ldexp(1.0, -k);
+            if (c.est < pick.est) pick = std::move(c);
+        }
+        if (pick.k > 0) {
+            std::vector<Block> rest_best;
+            {
+                std::vector<size_t> h = pick.head;
+                size_t pl = pick.placed;
+                rest_best = blocking_from(d, G, k_max, 2, true, ~0ull, h, pl);
+            }
+            for (int window : {0, 2}) {
+                std::vector<Block> r = beam_blocking(d, G, k_max, window, kBeamWidth, kBeamExpand, pick.head, pick.placed);
+                if ((!r.empty() || pick.placed == G) && r.size() < rest_best.size()) rest_best = std::move(r);
+            }
+            std::vector<Block> cand = pick.pre;
+            for (Block &b : rest_best) cand.push_back(std::move(b));
+            const double cost = zero_cost(d, cand, n, n - pick.k);
+            if (cost < best_cost) {
+                best = std::move(cand);
+                out.span = n - pick.k;
+                out.avoid = pick.X;
+            }
+        }
+    }
     out.gates.reserve(best.size());
     for (Block &b : best) out.gates.push_back(std::move(b.gates));
     return out;
@@ -226,13 +454,15 @@ void make_passes(int n, const std::vector<HostGate> &gates, const Blocking &b, i
             blk.push_back(&gates[gi]);
             for (int a = 0; a < gates[gi].nq; ++a) Q |= 1ull << gates[gi].q[a];
         }
+        for (int q = n - 1; q >= 0 && std::popcount(Q) < pad_to; --q)
+            if (!((b.avoid >> q) & 1)) Q |= 1ull << q;
         for (int q = n - 1; q >= 0 && std::popcount(Q) < pad_to; --q) Q |= 1ull << q;
         out->push_back(make_pass(pad_to > 0 ? PASS_TC : PASS_SIMT, Q, blk));
     }
 }
 
 void plan_fuse(int n, const std::vector<HostGate> &gates, int k_max, int pad_to, std::vector<Pass> *out) {
-    make_passes(n, gates, plan_blocks(n, gates, k_max), pad_to, out);
+    make_passes(n, gates, plan_blocks(n, gates, k_max, false), pad_to, out);
 }
 
 // Up to five qubits that share no block are placed on bits 0..4, chosen greedily
@@ -287,7 +517,7 @@ bool choose_layout(int n, const std::vector<HostGate> &gates, const Blocking &b,
 
 int plan_prefix(const Plan &plan, uint64_t *tmask) {
     const int n = plan.n;
-    const int max_sub = n - 4;
+    const int max_sub = plan.prefix_span > 0 ? plan.prefix_span : n - 4;
     uint64_t T = 0;
     int p = 0, need = 0;
     for (const Pass &q : plan.passes) {

@@ -60,7 +60,7 @@ def _plan_passes(plan):
 @pytest.mark.parametrize("precision,kmax,n", [(capi.RCS_PREC_FP32_FUSED, 2, 10), (capi.RCS_PREC_FP32_FUSED, 4, 10),
                                               (capi.RCS_PREC_FP32_FUSED, 5, 9), (capi.RCS_PREC_BF16X3, 0, 13),
                                               (capi.RCS_PREC_FP32_FUSED, 4, 14), (capi.RCS_PREC_FP32_PLAIN, 0, 9),
-                                              (capi.RCS_PREC_TF32X3, 0, 14)])
+                                              (capi.RCS_PREC_TF32X3, 0, 14), (capi.RCS_PREC_BF16X3, 0, 20)])
 def test_fused_plan_reproduces_circuit(oracle, lib, precision, kmax, n):
     """Applying the planned passes (FP64 matrices) with the oracle equals applying
     the circuit gate by gate with the oracle."""
@@ -139,3 +139,22 @@ def test_layout_keeps_low_bits_apart():
     assert sum(int(p != q) for q, p in enumerate(phys)) <= 10  # at most five transpositions
     for targets, _ in passes:
         assert sum(1 for t in targets if t < 5) <= 1, targets
+
+
+def test_zero_state_plan_uses_a_substate_prefix():
+    """A plan for a fresh state is chosen by cost with the sub-state prefix counted: on
+    the 34-qubit workload most of the early passes run on a sub-state of at most n - 2
+    qubits, leaving at most 30 full-state passes (greedy fewest-blocks planning: 37)."""
+    circ = C.config_circuit("34q_5x7m1_20cyc")
+    plan = capi.rcs_plan_build(34, circ.gates, capi.RCS_PREC_BF16X3)
+    try:
+        info, passes = _plan_passes(plan)
+    finally:
+        capi.rcs_plan_destroy(plan)
+    pre, m = info["prefix_passes"], info["prefix_qubits"]
+    assert pre >= 8 and 13 <= m <= 32
+    assert info["n_passes"] - pre <= 30
+    union = set()
+    for t, _ in passes[:pre]:
+        union |= set(int(x) for x in t)
+    assert len(union) <= m
