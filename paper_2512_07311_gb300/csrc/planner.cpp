@@ -26,25 +26,56 @@ static void left_multiply(std::vector<cd> &U, int k, const HostGate &g, const in
     const int gd = 1 << g.nq;
     uint32_t gmask = 0;
     for (int i = 0; i < g.nq; ++i) gmask |= 1u << pos[i];
-    for (int col = 0; col < d; ++col) {
-        for (int r0 = 0; r0 < d; ++r0) {
-            if (r0 & gmask) continue;
-            int rows[4];
-            cd v[4];
-            for (int j = 0; j < gd; ++j) {
-                int r = r0;
-                for (int i = 0; i < g.nq; ++i)
-                    if ((j >> i) & 1) r |= 1 << pos[i];
-                rows[j] = r;
-                v[j] = U[size_t(r) * d + col];
+    double mr[16], mi[16];
+    for (int e = 0; e < gd * gd; ++e) {
+        mr[e] = g.m[e].real();
+        mi[e] = g.m[e].imag();
+    }
+    double *u = reinterpret_cast<double *>(U.data());  // interleaved (re, im), row-major
+    for (int r0 = 0; r0 < d; ++r0) {
+        if (r0 & gmask) continue;
+        double *row[4];
+        for (int j = 0; j < gd; ++j) {
+            int r = r0;
+            for (int i = 0; i < g.nq; ++i)
+                if ((j >> i) & 1) r |= 1 << pos[i];
+            row[j] = u + size_t(r) * 2 * d;
+        }
+        for (int col = 0; col < d; ++col) {  // rows are contiguous: the inner loop streams them
+            double vr[4], vi[4];
+            for (int l = 0; l < gd; ++l) {
+                vr[l] = row[l][2 * col];
+                vi[l] = row[l][2 * col + 1];
             }
             for (int j = 0; j < gd; ++j) {
-                cd s = 0.0;
-                for (int l = 0; l < gd; ++l) s += g.m[j * gd + l] * v[l];
-                U[size_t(rows[j]) * d + col] = s;
+                double sr = 0.0, si = 0.0;
+                for (int l = 0; l < gd; ++l) {
+                    sr += mr[j * gd + l] * vr[l] - mi[j * gd + l] * vi[l];
+                    si += mr[j * gd + l] * vi[l] + mi[j * gd + l] * vr[l];
+                }
+                row[j][2 * col] = sr;
+                row[j][2 * col + 1] = si;
             }
         }
     }
+}
+
+// Runs f(0 .. count-1) on up to 16 host threads (each index once; f must only write
+// its own slot).
+template <class F>
+static void parallel_for(size_t count, F f) {
+    const size_t nt = std::min<size_t>(count, std::max(1u, std::min(16u, std::thread::hardware_concurrency())));
+    if (nt <= 1) {
+        for (size_t i = 0; i < count; ++i) f(i);
+        return;
+    }
+    std::vector<std::thread> pool;
+    pool.reserve(nt);
+    for (size_t t = 0; t < nt; ++t)
+        pool.emplace_back([&, t] {
+            for (size_t i = t; i < count; i += nt) f(i);
+        });
+    for (std::thread &th : pool) th.join();
 }
 
 static Pass make_pass(PassKind kind, uint64_t qmask, const std::vector<const HostGate *> &blk) {
@@ -84,12 +115,13 @@ struct Dag {
         }
         return true;
     }
+    // Ready gates in order of their lowest qubit (each visited once, from that qubit).
     void ready_gates(const std::vector<size_t> &head, std::vector<int> *out) const {
         out->clear();
         for (int q = 0; q < n; ++q) {
             if (head[q] >= queue[q].size()) continue;
             const int gi = queue[q][head[q]];
-            if (ready(gi, head) && std::find(out->begin(), out->end(), gi) == out->end()) out->push_back(gi);
+            if (std::countr_zero(mask[size_t(gi)]) == q && ready(gi, head)) out->push_back(gi);
         }
     }
     void take(int gi, std::vector<size_t> &head) const {
@@ -359,62 +391,77 @@ Blocking plan_blocks(int n, const std::vector<HostGate> &gates, int k_max, bool 
         d.mask[g] = m;
     }
     const int default_span = n - 4;
-    std::vector<Block> best = blocking(d, G, k_max, 0, false);
-    const std::pair<int, bool> variants[] = {{0, true}, {1, true}, {2, true}, {3, true}, {6, true}};
-    for (const auto &v : variants) {
-        if (G == 0) break;
-        std::vector<Block> b = blocking(d, G, k_max, v.first, v.second);
-        const bool better = from_zero ? zero_cost(d, b, n, default_span) < zero_cost(d, best, n, default_span)
-                                      : b.size() < best.size();
-        if (better) best = std::move(b);
+    // the greedy portfolio (the plain rule, then best-seed growth with affinity windows)
+    // and, for a run from |0...0>, the sub-state candidates run as one set of host tasks
+    const std::pair<int, bool> variants[] = {{0, false}, {0, true}, {1, true}, {2, true}, {3, true}, {6, true}};
+    const size_t nport = G ? std::size(variants) : 1;
+    std::vector<std::vector<Block>> port(nport);
+    const uint64_t full = n >= 64 ? ~0ull : ((1ull << n) - 1ull);
+    struct Cand {
+        double est = 1e300;
+        int k = 0;
+        uint64_t X = 0;
+        std::vector<Block> pre;
+        std::vector<size_t> head;
+        size_t placed = 0;
+    };
+    std::vector<Cand> cands(from_zero && G > 0 ? 4 : 0);
+    parallel_for(nport + cands.size(), [&](size_t task) {
+        if (task < nport) {
+            port[task] = blocking(d, G, k_max, variants[task].first, variants[task].second);
+            return;
+        }
+        const size_t ci = task - nport;
+        const int k = int(ci) + 2;
+        if (n - k < std::max(kTcK + 7, k_max)) return;
+        uint64_t X = 0;
+        for (int r = 0; r < k; ++r) {  // exclude the qubit that keeps the closure largest
+            size_t bsize = 0;
+            int bq = -1;
+            for (int q = 0; q < n; ++q) {
+                if ((X >> q) & 1) continue;
+                const size_t c = closure_size(gates, n, full & ~(X | (1ull << q)));
+                if (bq < 0 || c > bsize) {
+                    bsize = c;
+                    bq = q;
+                }
+            }
+            X |= 1ull << bq;
+        }
+        Cand c;
+        c.k = k;
+        c.X = X;
+        c.head.assign(size_t(n), 0);
+        c.pre = blocking_from(d, G, k_max, 2, true, full & ~X, c.head, c.placed);
+        std::vector<size_t> h = c.head;
+        size_t pl = c.placed;
+        const std::vector<Block> rest = blocking_from(d, G, k_max, 2, true, ~0ull, h, pl);
+        c.est = double(rest.size()) + double(c.pre.size()) * std::ldexp(1.0, -k);
+        cands[ci] = std::move(c);
+    });
+    std::vector<Block> best = std::move(port[0]);
+    for (size_t i = 1; i < port.size(); ++i) {
+        const bool better = from_zero ? zero_cost(d, port[i], n, default_span) < zero_cost(d, best, n, default_span)
+                                      : port[i].size() < best.size();
+        if (better) best = std::move(port[i]);
     }
     Blocking out;
     out.span = default_span;
     if (!from_zero) {
-        for (int window : {0, 2}) {
-            if (G == 0) break;
-            std::vector<Block> b =
-                beam_blocking(d, G, k_max, window, kBeamWidth, kBeamExpand, std::vector<size_t>(size_t(d.n), 0), 0);
-            if (!b.empty() && b.size() < best.size()) best = std::move(b);
+        if (G > 0) {
+            std::vector<std::vector<Block>> beams(2);
+            parallel_for(2, [&](size_t i) {
+                beams[i] = beam_blocking(d, G, k_max, i == 0 ? 0 : 2, kBeamWidth, kBeamExpand,
+                                         std::vector<size_t>(size_t(d.n), 0), 0);
+            });
+            for (std::vector<Block> &b : beams)
+                if (!b.empty() && b.size() < best.size()) best = std::move(b);
         }
     } else if (G > 0) {
-        const uint64_t full = n >= 64 ? ~0ull : ((1ull << n) - 1ull);
         double best_cost = zero_cost(d, best, n, default_span);
-        struct Cand {
-            double est = 1e300;
-            int k = 0;
-            uint64_t X = 0;
-            std::vector<Block> pre;
-            std::vector<size_t> head;
-            size_t placed = 0;
-        } pick;
-        for (int k = 2; k <= 5; ++k) {
-            if (n - k < std::max(kTcK + 7, k_max)) break;
-            uint64_t X = 0;
-            for (int r = 0; r < k; ++r) {  // exclude the qubit that keeps the closure largest
-                size_t bsize = 0;
-                int bq = -1;
-                for (int q = 0; q < n; ++q) {
-                    if ((X >> q) & 1) continue;
-                    const size_t c = closure_size(gates, n, full & ~(X | (1ull << q)));
-                    if (bq < 0 || c > bsize) {
-                        bsize = c;
-                        bq = q;
-                    }
-                }
-                X |= 1ull << bq;
-            }
-            Cand c;
-            c.k = k;
-            c.X = X;
-            c.head.assign(size_t(n), 0);
-            c.pre = blocking_from(d, G, k_max, 2, true, full & ~X, c.head, c.placed);
-            std::vector<size_t> h = c.head;
-            size_t pl = c.placed;
-            const std::vector<Block> rest = blocking_from(d, G, k_max, 2, true, ~0ull, h, pl);
-            c.est = double(rest.size()) + double(c.pre.size()) * std::ldexp(1.0, -k);
-            if (c.est < pick.est) pick = std::move(c);
-        }
+        Cand pick;
+        for (Cand &c : cands)
+            if (c.k > 0 && c.est < pick.est) pick = std::move(c);
         if (pick.k > 0) {
             std::vector<Block> rest_best;
             {
@@ -422,10 +469,12 @@ Blocking plan_blocks(int n, const std::vector<HostGate> &gates, int k_max, bool 
                 size_t pl = pick.placed;
                 rest_best = blocking_from(d, G, k_max, 2, true, ~0ull, h, pl);
             }
-            for (int window : {0, 2}) {
-                std::vector<Block> r = beam_blocking(d, G, k_max, window, kBeamWidth, kBeamExpand, pick.head, pick.placed);
+            std::vector<std::vector<Block>> beams(2);
+            parallel_for(2, [&](size_t i) {
+                beams[i] = beam_blocking(d, G, k_max, i == 0 ? 0 : 2, kBeamWidth, kBeamExpand, pick.head, pick.placed);
+            });
+            for (std::vector<Block> &r : beams)
                 if ((!r.empty() || pick.placed == G) && r.size() < rest_best.size()) rest_best = std::move(r);
-            }
             std::vector<Block> cand = pick.pre;
             for (Block &b : rest_best) cand.push_back(std::move(b));
             const double cost = zero_cost(d, cand, n, n - pick.k);
@@ -444,9 +493,9 @@ Blocking plan_blocks(int n, const std::vector<HostGate> &gates, int k_max, bool 
 // Passes for the blocks, each padded to pad_to qubits with the highest qubits it
 // does not use (identity on them).
 void make_passes(int n, const std::vector<HostGate> &gates, const Blocking &b, int pad_to, std::vector<Pass> *out) {
-    out->clear();
-    out->reserve(b.gates.size());
-    for (const std::vector<int> &blk_gates : b.gates) {
+    out->assign(b.gates.size(), Pass{});
+    parallel_for(b.gates.size(), [&](size_t bi) {
+        const std::vector<int> &blk_gates = b.gates[bi];
         uint64_t Q = 0;
         std::vector<const HostGate *> blk;
         blk.reserve(blk_gates.size());
@@ -457,8 +506,8 @@ void make_passes(int n, const std::vector<HostGate> &gates, const Blocking &b, i
         for (int q = n - 1; q >= 0 && std::popcount(Q) < pad_to; --q)
             if (!((b.avoid >> q) & 1)) Q |= 1ull << q;
         for (int q = n - 1; q >= 0 && std::popcount(Q) < pad_to; --q) Q |= 1ull << q;
-        out->push_back(make_pass(pad_to > 0 ? PASS_TC : PASS_SIMT, Q, blk));
-    }
+        (*out)[bi] = make_pass(pad_to > 0 ? PASS_TC : PASS_SIMT, Q, blk);
+    });
 }
 
 void plan_fuse(int n, const std::vector<HostGate> &gates, int k_max, int pad_to, std::vector<Pass> *out) {
