@@ -111,9 +111,10 @@ typedef struct {
     int32_t reserved;
     double hbm_bytes;     /* algorithmic HBM bytes: 16 * 2^n per pass */
     double flops;         /* algorithmic real flops of all passes (x3 for the split-precision path) */
-    int64_t prefix_passes; /* leading passes a run from |0...0> does on a compact sub-state (0: none) */
-    int32_t prefix_qubits; /* qubits of that sub-state */
-    int32_t reserved2;
+    int64_t prefix_passes; /* leading passes a run from |0...0> does on compact sub-states (0: none) */
+    int32_t prefix_qubits; /* qubits of the widest (last) sub-state */
+    int32_t prefix_stages; /* sub-states, nested and growing, each expanded into the next; the last
+                              expands into the full state */
 } rcs_plan_stats;
 
 /* ------------------------------------------------------------------ context */

@@ -199,21 +199,23 @@ int build_plan(rcs_ctx *ctx, int n, const std::vector<HostGate> &hg, const rcs_o
     plan->precision = o.precision;
     plan->n_gates = int64_t(hg.size());
     plan->phys_of.clear();
-    plan->prefix_span = 0;
+    plan->stage_spans.clear();
     // allow_layout: the plan is for a fresh state, so it may choose a layout and is
     // planned for a run from |0...0> (sub-state prefix counted)
     auto fused = [&](int k, int pad) {
         Blocking bl = plan_blocks(n, hg, k, allow_layout);
-        plan->prefix_span = bl.span;
+        plan->stage_spans = bl.spans;
         int phys[64];
         if (allow_layout && choose_layout(n, hg, bl, phys)) {
             std::vector<HostGate> moved = hg;
             for (HostGate &g : moved)
                 for (int a = 0; a < g.nq; ++a) g.q[a] = phys[g.q[a]];
-            uint64_t avoid = 0;
-            for (int q = 0; q < n; ++q)
-                if ((bl.avoid >> q) & 1) avoid |= 1ull << phys[q];
-            bl.avoid = avoid;
+            for (uint64_t &av : bl.avoid) {
+                uint64_t moved_av = 0;
+                for (int q = 0; q < n; ++q)
+                    if ((av >> q) & 1) moved_av |= 1ull << phys[q];
+                av = moved_av;
+            }
             make_passes(n, moved, bl, pad, &plan->passes);
             plan->phys_of.assign(phys, phys + n);
         } else {
@@ -346,11 +348,10 @@ int launch_one(rcs_ctx *c, float2 *psi, int n, const Pass &p, const uint8_t *ops
 // that one expansion pass writes out as the whole state.
 int run_passes(rcs_ctx *c, const Plan &plan, const uint8_t *d_ops, bool from_zero) {
     size_t first = 0;
-    uint64_t T = 0;
-    const int pre = from_zero ? plan_prefix(plan, &T) : 0;
+    std::vector<SubStage> stages;
+    const int pre = from_zero ? plan_stages(plan, &stages) : 0;
     if (pre > 0) {
-        const int m = std::popcount(T);
-        const size_t bytes = size_t(8) << m;
+        const size_t bytes = substage_bytes(stages);
         if (bytes > c->sub_cap) {
             RCS_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
             cudaFree(c->d_sub);
@@ -359,17 +360,8 @@ int run_passes(rcs_ctx *c, const Plan &plan, const uint8_t *d_ops, bool from_zer
             RCS_CUDA(c, cudaMalloc(&c->d_sub, bytes), "cudaMalloc sub-state");
             c->sub_cap = bytes;
         }
-        if (launch_init_zero(c->d_sub, m, c->stream) != RCS_OK)
-            return fail(c, RCS_ERR_CUDA, "sub-state reset: " + take_launch_error());
-        for (int i = 0; i < pre; ++i) {
-            const Pass q = compact_pass(plan.passes[i], T);
-            const uint8_t *ops = q.kind == PASS_TC ? d_ops + plan.tc_offset[i] : nullptr;
-            if (launch_one(c, c->d_sub, m, q, ops, plan_tf32(plan)) != RCS_OK)
-                return fail(c, RCS_ERR_CUDA, "launch of sub-state pass " + std::to_string(i) + " failed: " +
-                                                 take_launch_error());
-        }
-        if (launch_expand(c->psi, c->n, c->d_sub, T, c->stream) != RCS_OK)
-            return fail(c, RCS_ERR_CUDA, "expansion: " + take_launch_error());
+        if (run_substages(plan, stages, c->psi, c->d_sub, d_ops, c->d_err, c->stream) != RCS_OK)
+            return fail(c, RCS_ERR_CUDA, "sub-state stages: " + take_launch_error());
         c->zero_pending = false;
         first = size_t(pre);
     } else if (int rc = materialize(c); rc != RCS_OK) {
@@ -432,6 +424,49 @@ int plan_fresh_circuit(int n, const std::vector<HostGate> &gates, const rcs_opts
 }
 
 Pass substate_pass(const Pass &p, uint64_t T) { return compact_pass(p, T); }
+
+int launch_plan_pass(void *psi, int n, const Pass &p, const uint8_t *ops, int *d_err, void *stream, bool tf32) {
+    switch (p.kind) {
+        case PASS_1Q:
+        case PASS_2Q: return launch_pass_plain(psi, n, p, stream);
+        case PASS_SIMT: return launch_pass_simt(psi, n, p, stream);
+        case PASS_TC: return launch_pass_tc(psi, n, p, ops, d_err, stream, tf32);
+        default: return RCS_ERR_ARG;
+    }
+}
+
+int run_substages(const Plan &plan, const std::vector<SubStage> &stages, void *psi, void *sub, const uint8_t *d_ops,
+                  int *d_err, void *stream) {
+    const bool tf32 = plan_tf32(plan);
+    uint8_t *buf = static_cast<uint8_t *>(sub);
+    uint8_t *cur = nullptr;
+    uint64_t cur_mask = 0;
+    for (size_t si = 0; si < stages.size(); ++si) {
+        const SubStage &st = stages[si];
+        const int m = std::popcount(st.tmask);
+        uint8_t *next = buf;
+        buf += size_t(8) << m;
+        if (cur == nullptr) {
+            if (launch_init_zero(next, m, stream) != RCS_OK) return RCS_ERR_CUDA;
+        } else {  // the previous sub-state's qubits, numbered inside this one
+            uint64_t inner = 0;
+            for (int q = 0, k = 0; q < plan.n; ++q)
+                if ((st.tmask >> q) & 1) {
+                    if ((cur_mask >> q) & 1) inner |= 1ull << k;
+                    ++k;
+                }
+            if (launch_expand(next, m, cur, inner, stream) != RCS_OK) return RCS_ERR_CUDA;
+        }
+        for (int i = st.first; i < st.first + st.count; ++i) {
+            const Pass q = compact_pass(plan.passes[size_t(i)], st.tmask);
+            const uint8_t *ops = q.kind == PASS_TC ? d_ops + plan.tc_offset[size_t(i)] : nullptr;
+            if (launch_plan_pass(next, m, q, ops, d_err, stream, tf32) != RCS_OK) return RCS_ERR_CUDA;
+        }
+        cur = next;
+        cur_mask = st.tmask;
+    }
+    return launch_expand(psi, plan.n, cur, cur_mask, stream);
+}
 
 BitMap plan_to_stored(const Plan &plan) {
     BitMap m = identity_map(plan.n);
@@ -740,9 +775,10 @@ int rcs_plan_info(const rcs_plan *plan, rcs_plan_stats *out) {
     }
     out->k_max = kmax;
     out->hbm_bytes = 16.0 * amps * double(p.passes.size());
-    uint64_t T = 0;
-    out->prefix_passes = plan_prefix(p, &T);
-    out->prefix_qubits = out->prefix_passes ? std::popcount(T) : 0;
+    std::vector<SubStage> stages;
+    out->prefix_passes = plan_stages(p, &stages);
+    out->prefix_qubits = stages.empty() ? 0 : std::popcount(stages.back().tmask);
+    out->prefix_stages = int32_t(stages.size());
     return RCS_OK;
 }
 

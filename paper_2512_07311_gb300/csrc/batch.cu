@@ -208,9 +208,9 @@ struct InstHost {
     Plan plan;
     // tensor-core engine: operand images, sub-state prefix, layout maps
     uint8_t *d_ops = nullptr;
-    float2 *d_sub = nullptr;
+    void *d_sub = nullptr;
     int prefix = 0;
-    uint64_t tmask = 0;
+    std::vector<SubStage> stages;
     float2 *psi = nullptr;
     uint64_t *bsum = nullptr, *bpre = nullptr, *chunk = nullptr, *total = nullptr;
     uint64_t *d_bits = nullptr;  // shots
@@ -482,39 +482,25 @@ int launch_sampling(rcs_batch *b, InstHost &h, cudaStream_t st) {
     return RCS_OK;
 }
 
-int launch_pass(rcs_batch *b, const InstHost &h, float2 *psi, int n, const Pass &p, size_t i, cudaStream_t st) {
-    switch (p.kind) {
-        case PASS_1Q:
-        case PASS_2Q: return launch_pass_plain(psi, n, p, st);
-        case PASS_SIMT: return launch_pass_simt(psi, n, p, st);
-        case PASS_TC:
-            return launch_pass_tc(psi, n, p, h.d_ops + h.plan.tc_offset[i], b->d_err, st,
-                                  h.plan.precision == RCS_PREC_TF32X3);
-        default: return RCS_ERR_ARG;
-    }
-}
-
-// One circuit of the tensor-core engine: |0...0> (through the sub-state prefix when the
-// plan has one), every pass, then the sampler and XEB.
+// One circuit of the tensor-core engine: |0...0> (through the sub-state stages when the
+// plan has them), every pass, then the sampler and XEB.
 int record_chain(rcs_batch *b, InstHost &h, cudaStream_t st) {
     size_t first = 0;
     int rc = RCS_OK;
     if (h.prefix > 0) {
-        const int m = std::popcount(h.tmask);
-        if ((rc = launch_init_zero(h.d_sub, m, st)) != RCS_OK) return bfail(b, rc, "sub-state reset: " + take_launch_error());
-        for (int i = 0; i < h.prefix; ++i)
-            if ((rc = launch_pass(b, h, h.d_sub, m, substate_pass(h.plan.passes[size_t(i)], h.tmask), size_t(i), st)) !=
-                RCS_OK)
-                return bfail(b, rc, "sub-state pass: " + take_launch_error());
-        if ((rc = launch_expand(h.psi, h.n, h.d_sub, h.tmask, st)) != RCS_OK)
-            return bfail(b, rc, "expansion: " + take_launch_error());
+        if ((rc = run_substages(h.plan, h.stages, h.psi, h.d_sub, h.d_ops, b->d_err, st)) != RCS_OK)
+            return bfail(b, rc, "sub-state stages: " + take_launch_error());
         first = size_t(h.prefix);
     } else if ((rc = launch_init_zero(h.psi, h.n, st)) != RCS_OK) {
         return bfail(b, rc, "reset: " + take_launch_error());
     }
-    for (size_t i = first; i < h.plan.passes.size(); ++i)
-        if ((rc = launch_pass(b, h, h.psi, h.n, h.plan.passes[i], i, st)) != RCS_OK)
+    const bool tf32 = h.plan.precision == RCS_PREC_TF32X3;
+    for (size_t i = first; i < h.plan.passes.size(); ++i) {
+        const Pass &p = h.plan.passes[i];
+        const uint8_t *ops = p.kind == PASS_TC ? h.d_ops + h.plan.tc_offset[i] : nullptr;
+        if ((rc = launch_plan_pass(h.psi, h.n, p, ops, b->d_err, st, tf32)) != RCS_OK)
             return bfail(b, rc, "pass launch: " + take_launch_error());
+    }
     return launch_sampling(b, h, st);
 }
 
@@ -665,8 +651,8 @@ int rcs_batch_create(const rcs_batch_item *items, size_t n_items, const rcs_opts
                     BCUDA(b, cudaMalloc(&h.d_ops, img.size()), "operand images");
                     BCUDA(b, cudaMemcpy(h.d_ops, img.data(), img.size(), cudaMemcpyHostToDevice), "operand images");
                 }
-                h.prefix = plan_prefix(h.plan, &h.tmask);
-                if (h.prefix > 0) BCUDA(b, cudaMalloc(&h.d_sub, size_t(8) << std::popcount(h.tmask)), "sub-state");
+                h.prefix = plan_stages(h.plan, &h.stages);
+                if (h.prefix > 0) BCUDA(b, cudaMalloc(&h.d_sub, substage_bytes(h.stages)), "sub-state");
             }
             if (int rc = tc_prepare_device(); rc != RCS_OK) {
                 std::string m = take_launch_error();

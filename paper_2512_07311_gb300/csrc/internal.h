@@ -55,7 +55,7 @@ struct Plan {
     int k_max = 4;
     int64_t n_gates = 0;
     std::vector<Pass> passes;
-    int prefix_span = 0;  // widest sub-state of a run from |0...0> (0: n - 4)
+    std::vector<int> stage_spans;  // sub-state widths of a run from |0...0> (empty: one of n - 4)
     // device copies, per context device (uploaded lazily)
     int dev = -1;
     void *d_tc_ops = nullptr;   // hi/lo operand images of PASS_TC passes
@@ -70,8 +70,12 @@ void plan_fuse(int n, const std::vector<HostGate> &gates, int k_max, int pad_to,
 // how the qubits are labelled), then the passes for a gate list with those blocks.
 struct Blocking {
     std::vector<std::vector<int>> gates;  // gate indices of each block, in application order
-    int span = 0;        // run from |0...0>: leading blocks within `span` qubits use a sub-state
-    uint64_t avoid = 0;  // qubits that padding keeps out of blocks (those outside the sub-state)
+    // Run from |0...0>: stage s holds blocks [stage_end[s-1], stage_end[s]) and runs on a
+    // sub-state of at most spans[s] qubits (nested, growing); padding keeps its blocks off
+    // avoid[s], the qubits outside that sub-state. Empty: the default single stage (n - 4).
+    std::vector<int> spans;
+    std::vector<uint64_t> avoid;
+    std::vector<int> stage_end;
 };
 // from_zero: the blocks will run from |0...0>, so they are chosen by cost with the
 // sub-state prefix counted (see planner.cpp); otherwise by fewest blocks.
@@ -106,12 +110,25 @@ constexpr int kErrTimeout = 8;       // a bounded wait inside a kernel ran out
 int launch_init_zero(void *psi, int n, void *stream);
 int launch_expand(void *psi, int n, const void *sub, uint64_t tmask, void *stream);
 
-// Leading passes of a fused plan that a run from |0...0> can do on a compact
-// sub-state: the longest prefix whose targets span at most n - 4 qubits (each
-// sub-state pass then costs at most 1/16 of a full one), widened with untouched
-// qubits to the size the kernels need. Returns the pass count (0: not worth it)
-// and the qubit mask of the sub-state.
-int plan_prefix(const Plan &plan, uint64_t *tmask);
+// Leading passes of a fused plan that a run from |0...0> can do on compact
+// sub-states. Stage s takes the longest following run of passes whose targets, with
+// those of the earlier stages, span at most plan.stage_spans[s] qubits (n - 4 when no
+// spans are set), widened with untouched qubits to the size the kernels need. Stage
+// masks are nested. Returns the number of sub-state passes (0: not worth it).
+struct SubStage {
+    int first = 0, count = 0;  // passes [first, first + count)
+    uint64_t tmask = 0;        // qubits of the sub-state (cumulative over the stages)
+};
+int plan_stages(const Plan &plan, std::vector<SubStage> *stages);
+// Device bytes of the sub-state buffers of the stages (one after another).
+size_t substage_bytes(const std::vector<SubStage> &stages);
+// Runs the stages of a plan from |0...0> into psi (2^n amplitudes): reset of the first
+// sub-state, its passes, an expansion into the next sub-state, ..., and an expansion
+// into psi. `sub` holds substage_bytes(stages). Asynchronous; launch error text kept.
+int run_substages(const Plan &plan, const std::vector<SubStage> &stages, void *psi, void *sub,
+                  const uint8_t *d_ops, int *d_err, void *stream);
+// Launches one pass of a plan on a 2^n-amplitude state (ops: its operand image, if any).
+int launch_plan_pass(void *psi, int n, const Pass &p, const uint8_t *ops, int *d_err, void *stream, bool tf32);
 int launch_pass_plain(void *psi, int n, const Pass &p, void *stream);
 int launch_pass_simt(void *psi, int n, const Pass &p, void *stream);
 // Sets the tensor-core kernels' shared-memory attribute on the current device (once);

@@ -12,6 +12,7 @@
 #include <bit>
 #include <cmath>
 #include <cstring>
+#include <array>
 #include <map>
 #include <thread>
 
@@ -106,6 +107,15 @@ struct Dag {
     const std::vector<HostGate> *g;
     std::vector<std::vector<int>> queue;
     std::vector<uint64_t> mask;
+    std::vector<std::array<size_t, 2>> qpos;  // position of gate g in the queue of its qubit a
+
+    // placed under frontier `head`: every one of its qubits has moved past it
+    bool placed(size_t gi, const std::vector<size_t> &head) const {
+        const HostGate &x = (*g)[gi];
+        for (int a = 0; a < x.nq; ++a)
+            if (qpos[gi][size_t(a)] >= head[x.q[a]]) return false;
+        return true;
+    }
 
     bool ready(int gi, const std::vector<size_t> &head) const {
         const HostGate &x = (*g)[gi];
@@ -330,20 +340,40 @@ constexpr int kBeamExpand = 8;  // blocks grown per state and step
 
 namespace {
 
-// Gates that can run before any gate touching a qubit outside W: one scan in circuit
-// order (a gate is in iff it lies in W and none of its qubits has met a gate that
-// is out). Returns their number.
-size_t closure_size(const std::vector<HostGate> &gates, int n, uint64_t W) {
+// Gates not yet placed under frontier `head` that can run before any gate touching a
+// qubit outside W: one scan in circuit order (a gate is in iff it lies in W and none
+// of its qubits has met an unplaced gate that is out). Returns their number.
+size_t closure_size(const Dag &d, const std::vector<size_t> &head, uint64_t W) {
     uint64_t blocked = 0;
     size_t in = 0;
-    for (const HostGate &g : gates) {
-        uint64_t m = 0;
-        for (int a = 0; a < g.nq; ++a) m |= 1ull << g.q[a];
+    for (size_t gi = 0; gi < d.mask.size(); ++gi) {
+        if (d.placed(gi, head)) continue;
+        const uint64_t m = d.mask[gi];
         if ((m & ~W) == 0 && (m & blocked) == 0) ++in;
         else blocked |= m;
     }
-    (void)n;
     return in;
+}
+
+// Greedily picks k qubits of `pool` to leave out of the sub-state: each time the one
+// whose exclusion keeps the closure from `head` largest (lowest qubit on ties).
+uint64_t choose_excluded(const Dag &d, const std::vector<size_t> &head, int k, uint64_t pool, uint64_t full) {
+    uint64_t X = 0;
+    for (int r = 0; r < k; ++r) {
+        size_t bsize = 0;
+        int bq = -1;
+        for (int q = 0; q < d.n; ++q) {
+            if (!((pool >> q) & 1) || ((X >> q) & 1)) continue;
+            const size_t c = closure_size(d, head, full & ~(X | (1ull << q)));
+            if (bq < 0 || c > bsize) {
+                bsize = c;
+                bq = q;
+            }
+        }
+        if (bq < 0) break;
+        X |= 1ull << bq;
+    }
+    return X;
 }
 
 // Cost of a blocking run from |0...0>, in full-state passes: the leading blocks whose
@@ -367,13 +397,14 @@ double zero_cost(const Dag &d, const std::vector<Block> &b, int n, int span) {
 // Fuses the gates into blocks of at most k_max qubits. Several greedy blockings are
 // built -- the plain frontier rule, best-seed growth with affinity windows of 0, 1, 2,
 // 3 and 6 next gates, and a beam search -- and the one with the fewest blocks is kept.
-// For a run from |0...0> (from_zero) the choice is by cost instead, and a second kind
-// of candidate is added: for k = 2..5 excluded qubits (chosen greedily to keep the
-// largest closure, the gates that precede every gate on them), the closure is blocked
-// inside the other n - k qubits, where its passes run on a 2^(n-k) sub-state, and the
-// rest of the circuit is blocked after it (greedily to pick k, then by beam search).
-// On the 34-qubit 20-cycle workload at k = 6 this takes the full-state passes from
-// 37 (45 passes, 8 of them on a 30-qubit sub-state) to 27 (16 more on a 31-qubit one).
+// For a run from |0...0> (from_zero) the choice is by cost instead (full passes plus
+// sub-state passes x 2^(width - n)), and staged candidates are added. For a single
+// stage of k = 2..5 excluded qubits, or two nested stages (k1 then k2 < k1 excluded),
+// the excluded qubits are chosen greedily to keep the largest closure (the gates that
+// precede every gate on them). Each stage's closure is blocked inside its sub-state,
+// and the rest of the circuit after it (greedily to pick the candidate, then by beam
+// search). On the 34-qubit 20-cycle workload at k = 6 this takes the full-state passes
+// from 37 (45 passes, 8 of them on a 30-qubit sub-state) to 27.
 Blocking plan_blocks(int n, const std::vector<HostGate> &gates, int k_max, bool from_zero) {
     const size_t G = gates.size();
     k_max = std::max(2, std::min(k_max, n));
@@ -382,62 +413,71 @@ Blocking plan_blocks(int n, const std::vector<HostGate> &gates, int k_max, bool 
     d.g = &gates;
     d.queue.assign(n, {});
     d.mask.resize(G);
+    d.qpos.resize(G);
     for (size_t g = 0; g < G; ++g) {
         uint64_t m = 0;
         for (int a = 0; a < gates[g].nq; ++a) {
+            d.qpos[g][size_t(a)] = d.queue[gates[g].q[a]].size();
             d.queue[gates[g].q[a]].push_back(int(g));
             m |= 1ull << gates[g].q[a];
         }
         d.mask[g] = m;
     }
     const int default_span = n - 4;
-    // the greedy portfolio (the plain rule, then best-seed growth with affinity windows)
-    // and, for a run from |0...0>, the sub-state candidates run as one set of host tasks
-    const std::pair<int, bool> variants[] = {{0, false}, {0, true}, {1, true}, {2, true}, {3, true}, {6, true}};
-    const size_t nport = G ? std::size(variants) : 1;
-    std::vector<std::vector<Block>> port(nport);
     const uint64_t full = n >= 64 ? ~0ull : ((1ull << n) - 1ull);
+    // staged candidates: k excluded qubits per stage, nested and shrinking
     struct Cand {
-        double est = 1e300;
-        int k = 0;
-        uint64_t X = 0;
+        double est = 1e300;  // greedy rest + sub-state cost
+        double sub_cost = 0.0;
+        std::vector<int> ks;
+        std::vector<uint64_t> X;
+        std::vector<int> stage_end;
         std::vector<Block> pre;
         std::vector<size_t> head;
         size_t placed = 0;
     };
-    std::vector<Cand> cands(from_zero && G > 0 ? 4 : 0);
+    std::vector<std::vector<int>> configs;
+    if (from_zero && G > 0) {
+        const int min_sub = std::max(kTcK + 7, k_max);
+        for (int k = 2; k <= 5; ++k)
+            if (n - k >= min_sub) configs.push_back({k});
+        const int pairs[][2] = {{4, 2}, {5, 2}, {6, 2}, {4, 3}, {5, 3}, {6, 3}, {7, 3}, {6, 4}, {7, 4}};
+        for (const auto &pr : pairs)
+            if (n - pr[0] >= min_sub) configs.push_back({pr[0], pr[1]});
+    }
+    // the greedy portfolio (the plain rule, then best-seed growth with affinity windows)
+    // and the staged candidates run as one set of host tasks
+    const std::pair<int, bool> variants[] = {{0, false}, {0, true}, {1, true}, {2, true}, {3, true}, {6, true}};
+    const size_t nport = G ? std::size(variants) : 1;
+    std::vector<std::vector<Block>> port(nport);
+    std::vector<Cand> cands(configs.size());
     parallel_for(nport + cands.size(), [&](size_t task) {
         if (task < nport) {
             port[task] = blocking(d, G, k_max, variants[task].first, variants[task].second);
             return;
         }
-        const size_t ci = task - nport;
-        const int k = int(ci) + 2;
-        if (n - k < std::max(kTcK + 7, k_max)) return;
-        uint64_t X = 0;
-        for (int r = 0; r < k; ++r) {  // exclude the qubit that keeps the closure largest
-            size_t bsize = 0;
-            int bq = -1;
-            for (int q = 0; q < n; ++q) {
-                if ((X >> q) & 1) continue;
-                const size_t c = closure_size(gates, n, full & ~(X | (1ull << q)));
-                if (bq < 0 || c > bsize) {
-                    bsize = c;
-                    bq = q;
-                }
-            }
-            X |= 1ull << bq;
-        }
+        const std::vector<int> &ks = configs[task - nport];
         Cand c;
-        c.k = k;
-        c.X = X;
+        c.ks = ks;
         c.head.assign(size_t(n), 0);
-        c.pre = blocking_from(d, G, k_max, 2, true, full & ~X, c.head, c.placed);
+        uint64_t pool = full;
+        double sub_cost = 0.0;
+        for (size_t si = 0; si < ks.size(); ++si) {
+            const uint64_t X = choose_excluded(d, c.head, ks[si], pool, full);
+            std::vector<Block> b = blocking_from(d, G, k_max, 2, true, full & ~X, c.head, c.placed);
+            sub_cost += double(b.size()) * std::ldexp(1.0, -ks[si]);
+            if (si > 0) sub_cost += 0.5 * std::ldexp(1.0, -ks[si]);  // expansion into this sub-state
+            for (Block &x : b) c.pre.push_back(std::move(x));
+            c.stage_end.push_back(int(c.pre.size()));
+            c.X.push_back(X);
+            pool = X;
+        }
         std::vector<size_t> h = c.head;
         size_t pl = c.placed;
         const std::vector<Block> rest = blocking_from(d, G, k_max, 2, true, ~0ull, h, pl);
-        c.est = double(rest.size()) + double(c.pre.size()) * std::ldexp(1.0, -k);
-        cands[ci] = std::move(c);
+        c.sub_cost = sub_cost;
+        c.est = double(rest.size()) + sub_cost;
+        cands[task - nport] = std::move(c);
     });
     std::vector<Block> best = std::move(port[0]);
     for (size_t i = 1; i < port.size(); ++i) {
@@ -446,7 +486,6 @@ Blocking plan_blocks(int n, const std::vector<HostGate> &gates, int k_max, bool 
         if (better) best = std::move(port[i]);
     }
     Blocking out;
-    out.span = default_span;
     if (!from_zero) {
         if (G > 0) {
             std::vector<std::vector<Block>> beams(2);
@@ -457,31 +496,32 @@ Blocking plan_blocks(int n, const std::vector<HostGate> &gates, int k_max, bool 
             for (std::vector<Block> &b : beams)
                 if (!b.empty() && b.size() < best.size()) best = std::move(b);
         }
-    } else if (G > 0) {
-        double best_cost = zero_cost(d, best, n, default_span);
-        Cand pick;
-        for (Cand &c : cands)
-            if (c.k > 0 && c.est < pick.est) pick = std::move(c);
-        if (pick.k > 0) {
-            std::vector<Block> rest_best;
-            {
-                std::vector<size_t> h = pick.head;
-                size_t pl = pick.placed;
-                rest_best = blocking_from(d, G, k_max, 2, true, ~0ull, h, pl);
-            }
-            std::vector<std::vector<Block>> beams(2);
-            parallel_for(2, [&](size_t i) {
-                beams[i] = beam_blocking(d, G, k_max, i == 0 ? 0 : 2, kBeamWidth, kBeamExpand, pick.head, pick.placed);
-            });
-            for (std::vector<Block> &r : beams)
-                if ((!r.empty() || pick.placed == G) && r.size() < rest_best.size()) rest_best = std::move(r);
-            std::vector<Block> cand = pick.pre;
-            for (Block &b : rest_best) cand.push_back(std::move(b));
-            const double cost = zero_cost(d, cand, n, n - pick.k);
-            if (cost < best_cost) {
-                best = std::move(cand);
-                out.span = n - pick.k;
-                out.avoid = pick.X;
+    } else if (!cands.empty()) {
+        const double best_cost = zero_cost(d, best, n, default_span);
+        size_t pi = 0;
+        for (size_t i = 1; i < cands.size(); ++i)
+            if (cands[i].est < cands[pi].est) pi = i;
+        Cand &pick = cands[pi];
+        std::vector<Block> rest_best;
+        {
+            std::vector<size_t> h = pick.head;
+            size_t pl = pick.placed;
+            rest_best = blocking_from(d, G, k_max, 2, true, ~0ull, h, pl);
+        }
+        std::vector<std::vector<Block>> beams(2);
+        parallel_for(2, [&](size_t i) {
+            beams[i] = beam_blocking(d, G, k_max, i == 0 ? 0 : 2, kBeamWidth, kBeamExpand, pick.head, pick.placed);
+        });
+        for (std::vector<Block> &r : beams)
+            if ((!r.empty() || pick.placed == G) && r.size() < rest_best.size()) rest_best = std::move(r);
+        const double cost = pick.sub_cost + double(rest_best.size());
+        if (cost < best_cost) {
+            best = std::move(pick.pre);
+            for (Block &b : rest_best) best.push_back(std::move(b));
+            for (size_t si = 0; si < pick.ks.size(); ++si) {
+                out.spans.push_back(n - pick.ks[si]);
+                out.avoid.push_back(pick.X[si]);
+                out.stage_end.push_back(pick.stage_end[si]);
             }
         }
     }
@@ -503,8 +543,14 @@ void make_passes(int n, const std::vector<HostGate> &gates, const Blocking &b, i
             blk.push_back(&gates[gi]);
             for (int a = 0; a < gates[gi].nq; ++a) Q |= 1ull << gates[gi].q[a];
         }
+        uint64_t avoid = 0;  // padding stays inside the block's sub-state
+        for (size_t si = 0; si < b.stage_end.size(); ++si)
+            if (bi < size_t(b.stage_end[si])) {
+                avoid = b.avoid[si];
+                break;
+            }
         for (int q = n - 1; q >= 0 && std::popcount(Q) < pad_to; --q)
-            if (!((b.avoid >> q) & 1)) Q |= 1ull << q;
+            if (!((avoid >> q) & 1)) Q |= 1ull << q;
         for (int q = n - 1; q >= 0 && std::popcount(Q) < pad_to; --q) Q |= 1ull << q;
         (*out)[bi] = make_pass(pad_to > 0 ? PASS_TC : PASS_SIMT, Q, blk);
     });
@@ -564,25 +610,52 @@ bool choose_layout(int n, const std::vector<HostGate> &gates, const Blocking &b,
     return !up.empty();
 }
 
-int plan_prefix(const Plan &plan, uint64_t *tmask) {
+int plan_stages(const Plan &plan, std::vector<SubStage> *stages) {
+    stages->clear();
     const int n = plan.n;
-    const int max_sub = plan.prefix_span > 0 ? plan.prefix_span : n - 4;
+    std::vector<int> spans = plan.stage_spans;
+    if (spans.empty()) spans.push_back(n - 4);
     uint64_t T = 0;
-    int p = 0, need = 0;
-    for (const Pass &q : plan.passes) {
-        if (q.kind != PASS_TC && q.kind != PASS_SIMT) break;
-        uint64_t m = 0;
-        for (int i = 0; i < q.k; ++i) m |= 1ull << q.t[i];
-        if (std::popcount(T | m) > max_sub) break;
-        T |= m;
-        need = std::max(need, q.kind == PASS_TC ? kTcK + 7 : q.k);
-        ++p;
+    size_t p = 0;
+    int need = 0, total = 0;
+    for (const int span : spans) {
+        if (span >= n) break;
+        SubStage st;
+        st.first = int(p);
+        while (p < plan.passes.size()) {
+            const Pass &q = plan.passes[p];
+            if (q.kind != PASS_TC && q.kind != PASS_SIMT) break;
+            uint64_t Tn = T;
+            for (int i = 0; i < q.k; ++i) Tn |= 1ull << q.t[i];
+            if (std::popcount(Tn) > span) break;
+            T = Tn;
+            need = std::max(need, q.kind == PASS_TC ? kTcK + 7 : q.k);
+            ++p;
+        }
+        // widened, after its passes, with idle |0> qubits to the size the kernels need
+        for (int b = 0; b < n && std::popcount(T) < need; ++b) T |= 1ull << b;
+        if (std::popcount(T) >= n) {
+            stages->clear();
+            return 0;
+        }
+        st.count = int(p) - st.first;
+        st.tmask = T;
+        if (st.count > 0) {
+            stages->push_back(st);
+            total += st.count;
+        }
     }
-    if (p < 2) return 0;
-    for (int q = 0; q < n && std::popcount(T) < need; ++q) T |= 1ull << q;  // idle |0> qubits
-    if (std::popcount(T) > max_sub) return 0;
-    *tmask = T;
-    return p;
+    if (total < 2) {
+        stages->clear();
+        return 0;
+    }
+    return total;
+}
+
+size_t substage_bytes(const std::vector<SubStage> &stages) {
+    size_t b = 0;
+    for (const SubStage &s : stages) b += size_t(8) << std::popcount(s.tmask);
+    return b;
 }
 
 void plan_plain(int n, const std::vector<HostGate> &gates, std::vector<Pass> *out) {

@@ -196,7 +196,8 @@ def test_substate_prefix_vs_oracle(lib, oracle, precision):
     circ = C.generate(C.grid_for_n(n), cycles=10, pattern="ABCDCDAB", seed=91, jitter=0.05)
     plan = capi.rcs_plan_build(n, circ.gates, precision)
     info = capi.rcs_plan_info(plan)
-    assert info["prefix_passes"] >= 2 and info["prefix_qubits"] <= n - 4
+    assert info["prefix_passes"] >= 2 and info["prefix_qubits"] <= n - 2
+    assert info["prefix_stages"] == 2  # nested sub-states, each expanded into the next
     ctx = capi.rcs_create(n, precision)
     try:
         capi.rcs_plan_upload(ctx, plan)
