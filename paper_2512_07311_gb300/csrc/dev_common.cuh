@@ -32,11 +32,19 @@ __device__ __forceinline__ uint64_t fx_sq(float x, int &bad) {
     if (e) m |= 0x800000u;
     else e = 1;
     if (e >= 128u) bad = 1;
-    const uint64_t m2 = uint64_t(m) * uint64_t(m);  // < 2^48; x^2 * 2^62 = m2 * 2^(2e - 238)
-    const int sh = 2 * int(e) - 238;
+    const int sh = 2 * int(e) - 238;  // x^2 * 2^62 = m^2 * 2^sh, m^2 < 2^48
+    if (sh <= -18) {
+        // r = -sh >= 18 (|x| < 2^-8, the usual case): the result is below 2^31, so
+        // floor(m^2 / 2^(r-1)) = floor(floor(m^2 / 2^16) / 2^(r-17)) in 32-bit integers,
+        // with floor(m^2 / 2^16) the high word of (m * 2^8)^2
+        const int r = -sh;
+        if (r > 48) return 0ull;
+        const uint32_t a = m << 8;
+        return uint64_t(((__umulhi(a, a) >> (r - 17)) + 1u) >> 1);  // round half up
+    }
+    const uint64_t m2 = uint64_t(m) * uint64_t(m);
     if (sh >= 0) return sh <= 16 ? (m2 << sh) : 0ull;
     const int r = -sh;
-    if (r > 48) return 0ull;
     return ((m2 >> (r - 1)) + 1ull) >> 1;  // round half up
 }
 
