@@ -246,7 +246,13 @@ def run_batch(args, torch, capi):
             pi = capi.rcs_plan_info(plan)
             capi.rcs_plan_destroy(plan)
             pre, m = pi["prefix_passes"], pi["prefix_qubits"]
-            total += 16.0 * 2**n * (pi["n_passes"] - pre) + 16.0 * 2**m * pre + 8.0 * 2**n + (8.0 * 2**m if pre else 0)
+            # sub-state passes (counted at the widest sub-state), then the first full pass reading
+            # the last sub-state (8 x 2^m in, 8 x 2^n out) and the other full passes; no prefix:
+            # reset (8 x 2^n) and full passes
+            if pre:
+                total += 16.0 * 2**m * pre + 8.0 * 2**m + 8.0 * 2**n + 16.0 * 2**n * (pi["n_passes"] - pre - 1)
+            else:
+                total += 8.0 * 2**n + 16.0 * 2**n * pi["n_passes"]
         return total
 
     prec = capi.PRECISIONS[args.precision]
@@ -363,6 +369,7 @@ def main():
             # waits for those passes only (the sampler of this step keeps running)
             ms_p, full = capi.rcs_last_pass_timing(ctx)
             pass_ms.append(ms_p)
+            timed_full = full
         t_end.record(stream)
         barrier()
     total_ms = t_start.elapsed_time(t_end)
@@ -378,8 +385,17 @@ def main():
     peaks = measured_peaks()
     passes = int(info["n_passes"])
     prefix = int(info["prefix_passes"])
-    full_passes = passes - prefix
+    # the library times the full-state passes; the first full pass may run fused with the
+    # expansion of the last sub-state, before the timed region of the passes
+    full_passes = timed_full
     t_pass_s = statistics.median(pass_ms) / 1e3 / full_passes
+    # launches per step: sub-state reset, expansions between sub-states, the final expansion
+    # unless the first full pass reads the last sub-state, every pass, block sums, the 3-phase
+    # scan, the sampler and the 2-phase XEB
+    stages = int(info["prefix_stages"])
+    fused = prefix > 0 and full_passes == passes - prefix - 1
+    setup = 1 + max(stages - 1, 0) + (0 if (prefix == 0 or fused) else 1)
+    gpu_launches = passes + setup + 1 + 3 + 1 + 2
     bytes_per_launch = 16.0 * 2.0**n
     achieved = bytes_per_launch / t_pass_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -468,7 +484,7 @@ def main():
             "roofline": roofline,
             "e2e": {"value": statistics.median(e2e_ms) / 1e3, "unit": "s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": (passes + (2 if prefix else 1)) + 1 + 3 + 1 + 2,
+            "gpu_launches": gpu_launches,
             "clocks": clocks,
             "compare": compare,
             "cpu_baseline": cpu,

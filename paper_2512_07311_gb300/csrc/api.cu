@@ -360,10 +360,11 @@ int run_passes(rcs_ctx *c, const Plan &plan, const uint8_t *d_ops, bool from_zer
             RCS_CUDA(c, cudaMalloc(&c->d_sub, bytes), "cudaMalloc sub-state");
             c->sub_cap = bytes;
         }
-        if (run_substages(plan, stages, c->psi, c->d_sub, d_ops, c->d_err, c->stream) != RCS_OK)
+        int fused = 0;
+        if (run_substages(plan, stages, c->psi, c->d_sub, d_ops, c->d_err, c->stream, &fused) != RCS_OK)
             return fail(c, RCS_ERR_CUDA, "sub-state stages: " + take_launch_error());
         c->zero_pending = false;
-        first = size_t(pre);
+        first = size_t(pre + fused);
     } else if (int rc = materialize(c); rc != RCS_OK) {
         return rc;
     }
@@ -436,8 +437,9 @@ int launch_plan_pass(void *psi, int n, const Pass &p, const uint8_t *ops, int *d
 }
 
 int run_substages(const Plan &plan, const std::vector<SubStage> &stages, void *psi, void *sub, const uint8_t *d_ops,
-                  int *d_err, void *stream) {
+                  int *d_err, void *stream, int *fused) {
     const bool tf32 = plan_tf32(plan);
+    *fused = 0;
     uint8_t *buf = static_cast<uint8_t *>(sub);
     uint8_t *cur = nullptr;
     uint64_t cur_mask = 0;
@@ -464,6 +466,13 @@ int run_substages(const Plan &plan, const std::vector<SubStage> &stages, void *p
         }
         cur = next;
         cur_mask = st.tmask;
+    }
+    const size_t after = size_t(stages.back().first + stages.back().count);
+    if (after < plan.passes.size() && tc_pass_takes_substate(plan.passes[after], plan.n)) {
+        const int rc = launch_pass_tc_from_sub(psi, plan.n, plan.passes[after], d_ops + plan.tc_offset[after], d_err,
+                                               stream, tf32, cur, cur_mask);
+        if (rc == RCS_OK) *fused = 1;
+        return rc;
     }
     return launch_expand(psi, plan.n, cur, cur_mask, stream);
 }

@@ -488,9 +488,10 @@ int record_chain(rcs_batch *b, InstHost &h, cudaStream_t st) {
     size_t first = 0;
     int rc = RCS_OK;
     if (h.prefix > 0) {
-        if ((rc = run_substages(h.plan, h.stages, h.psi, h.d_sub, h.d_ops, b->d_err, st)) != RCS_OK)
+        int fused = 0;
+        if ((rc = run_substages(h.plan, h.stages, h.psi, h.d_sub, h.d_ops, b->d_err, st, &fused)) != RCS_OK)
             return bfail(b, rc, "sub-state stages: " + take_launch_error());
-        first = size_t(h.prefix);
+        first = size_t(h.prefix + fused);
     } else if ((rc = launch_init_zero(h.psi, h.n, st)) != RCS_OK) {
         return bfail(b, rc, "reset: " + take_launch_error());
     }

@@ -123,10 +123,12 @@ int plan_stages(const Plan &plan, std::vector<SubStage> *stages);
 // Device bytes of the sub-state buffers of the stages (one after another).
 size_t substage_bytes(const std::vector<SubStage> &stages);
 // Runs the stages of a plan from |0...0> into psi (2^n amplitudes): reset of the first
-// sub-state, its passes, an expansion into the next sub-state, ..., and an expansion
-// into psi. `sub` holds substage_bytes(stages). Asynchronous; launch error text kept.
+// sub-state, its passes, an expansion into the next sub-state, ..., and either an
+// expansion into psi or, when the next pass can read a sub-state, that pass taking the
+// last sub-state as input (*fused = 1: the caller resumes one pass later). `sub` holds
+// substage_bytes(stages). Asynchronous; launch error text kept.
 int run_substages(const Plan &plan, const std::vector<SubStage> &stages, void *psi, void *sub,
-                  const uint8_t *d_ops, int *d_err, void *stream);
+                  const uint8_t *d_ops, int *d_err, void *stream, int *fused);
 // Launches one pass of a plan on a 2^n-amplitude state (ops: its operand image, if any).
 int launch_plan_pass(void *psi, int n, const Pass &p, const uint8_t *ops, int *d_err, void *stream, bool tf32);
 int launch_pass_plain(void *psi, int n, const Pass &p, void *stream);
@@ -136,6 +138,13 @@ int launch_pass_simt(void *psi, int n, const Pass &p, void *stream);
 int tc_prepare_device();
 // tf32: the TF32x3 kernel (operand image from tc_build_ops(p, img, true)), else BF16x3.
 int launch_pass_tc(void *psi, int n, const Pass &p, const void *d_ops, int *d_err, void *stream, bool tf32);
+// The same pass reading its input from a sub-state instead of psi: the state is |0> on
+// the qubits outside tmask, and sub holds its amplitudes with those qubits at 0 at their
+// compact index; the pass writes the whole 2^n state to psi (an expansion and a pass in
+// one). tc_pass_takes_substate says whether a pass can run this way (slice-order kernel).
+bool tc_pass_takes_substate(const Pass &p, int n);
+int launch_pass_tc_from_sub(void *psi, int n, const Pass &p, const void *d_ops, int *d_err, void *stream, bool tf32,
+                            const void *sub, uint64_t tmask);
 
 // Size in bytes of the operand image of one 6-qubit pass (BF16x3: 64 KB, TF32x3:
 // 96 KB), and its builder.

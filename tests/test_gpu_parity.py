@@ -198,12 +198,17 @@ def test_substate_prefix_vs_oracle(lib, oracle, precision):
     info = capi.rcs_plan_info(plan)
     assert info["prefix_passes"] >= 2 and info["prefix_qubits"] <= n - 2
     assert info["prefix_stages"] == 2  # nested sub-states, each expanded into the next
+    # a tensor-core pass after the sub-states reads the last sub-state itself (expansion and
+    # pass in one launch) unless it needs the memory-order kernel (4+ targets below bit 5)
+    t_next, _ = capi.rcs_plan_pass(plan, info["prefix_passes"])
+    fuses = precision != capi.RCS_PREC_FP32_FUSED and sum(int(x) < 5 for x in t_next) < 4
+    assert fuses == (precision != capi.RCS_PREC_FP32_FUSED)
     ctx = capi.rcs_create(n, precision)
     try:
         capi.rcs_plan_upload(ctx, plan)
         capi.rcs_plan_run(ctx, plan)
         ms, full = capi.rcs_last_pass_timing(ctx)
-        assert full == info["n_passes"] - info["prefix_passes"] and ms > 0
+        assert full == info["n_passes"] - info["prefix_passes"] - int(fuses) and ms > 0
         got = capi.rcs_state_read(ctx)
     finally:
         capi.rcs_destroy(ctx)
