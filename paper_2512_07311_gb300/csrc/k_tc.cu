@@ -449,21 +449,52 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
         // ---------------------------------------------------------------- loaders (slice order)
         const int q = warp & 3, h = warp >> 2;  // TMEM lane quarter, amplitude half
         const int srow = 32 * q + lane;          // slice within the tile = TMEM lane
+        // kSub: bit i of the slice index s sits on the i-th lowest non-target qubit p_i; its
+        // place in the sub-state is c(p_i) = the rank of p_i in tmask, or none (the slice is
+        // then all zeros). The 7 row bits of this thread's slice are folded once here; tile
+        // bit L is this lane's job for lane L, combined over the warp per tile.
+        uint64_t row_cb = 0;
+        bool row_z = false;
+        int lane_c = -1;
+        if constexpr (kSub) {
+            auto place = [&](int pos) {
+                return ((a.tmask >> pos) & 1ull) ? __popcll(a.tmask & ((1ull << pos) - 1ull)) : -1;
+            };
+            for (int qb = 0, i = 0; qb < 64 && i < 7 + 32; ++qb) {
+                bool tgt = false;
+#pragma unroll
+                for (int x = 0; x < K; ++x) tgt |= (t[x] == qb);
+                if (tgt) continue;
+                const int c = place(qb);
+                if (i < 7) {
+                    if ((srow >> i) & 1) {
+                        if (c < 0) row_z = true;
+                        else row_cb |= 1ull << c;
+                    }
+                } else if (i - 7 == lane) {
+                    lane_c = c;
+                }
+                ++i;
+            }
+        }
         auto issue = [&](uint32_t i, int b) {
             const uint64_t tile = uint64_t(blockIdx.x) + uint64_t(i) * gridDim.x;
             const uint64_t base = slice_base(tile * M + srow, t);
             if constexpr (kSub) {
                 // a slice with a qubit outside the sub-state set is all zeros; otherwise amplitude
-                // j is at compact index pext(base) | pext(off[j]) unless off[j] leaves the sub-state.
-                // Zeros come from copies of 0 source bytes (no read): this keeps the loader paced
-                // like a normal pass (skipping them measured slower, 76 vs 56 ms at 34 qubits)
-                const bool zslice = (base & ~a.tmask) != 0;
-                uint64_t cb = 0;
-                int k = 0;
-                for (uint64_t m = zslice ? 0ull : a.tmask; m; m &= m - 1, ++k) {
-                    const int bpos = __ffsll(static_cast<long long>(m)) - 1;
-                    cb |= ((base >> bpos) & 1ull) << k;
+                // j is at compact index (row and tile parts of the slice) | pext(off[j]) unless
+                // off[j] leaves the sub-state. Zeros come from copies of 0 source bytes (no read):
+                // this keeps the loader paced like a normal pass (skipping them measured slower)
+                const bool tbit = (tile >> lane) & 1ull;
+                uint64_t cb = (tbit && lane_c >= 0) ? (1ull << lane_c) : 0ull;
+                uint32_t zt = (tbit && lane_c < 0) ? 1u : 0u;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    cb |= __shfl_xor_sync(0xffffffffu, cb, o);
+                    zt |= __shfl_xor_sync(0xffffffffu, zt, o);
                 }
+                cb |= row_cb;
+                const bool zslice = row_z || zt != 0;
 #pragma unroll 8
                 for (int jj = 0; jj < 32; ++jj) {
                     const int j = 32 * h + jj;
