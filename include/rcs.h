@@ -290,7 +290,7 @@ typedef struct {
  *   BF16X3 or TF32X3: every circuit is planned like rcs_apply_circuit on a fresh
  *     state (fused 6-qubit tensor-core passes, its own qubit layout and sub-state
  *     prefix; circuits under 13 qubits get FP32 fused passes). The graph holds one
- *     chain of launches per circuit on up to 32 parallel branches. opts->k_max must
+ *     chain of launches per circuit on up to 64 parallel branches. opts->k_max must
  *     be 0 or 6.
  * Samples, XEB and rcs_batch_state_read use each circuit's own qubit numbering in
  * either engine. */

@@ -22,7 +22,7 @@
 // Tensor-core engine (precision BF16X3 or TF32X3). Each circuit is planned like a
 // single one (fused 6-qubit passes, its own qubit layout and sub-state prefix), and the
 // graph holds one chain of launches per circuit -- reset or prefix and expansion, the
-// tensor-core passes, then the sampler and XEB -- on up to 32 parallel branches. A
+// tensor-core passes, then the sampler and XEB -- on up to 64 parallel branches. A
 // tensor-core pass needs a whole SM (one 17-warp CTA with ~200 KB of shared memory
 // and 512 tensor-memory columns), so the passes of different circuits cannot share one
 // persistent kernel the way the FP32 items do; the graph's branches let the passes of
@@ -661,7 +661,7 @@ int rcs_batch_create(const rcs_batch_item *items, size_t n_items, const rcs_opts
                 return set_thread_error(rc, m);
             }
             BCUDA(b, cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "stream");
-            const size_t nside = std::min<size_t>(32, n_items);
+            const size_t nside = std::min<size_t>(64, n_items);
             b->side.resize(nside, nullptr);
             for (auto &s : b->side) BCUDA(b, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "stream");
             b->ev.resize(1 + nside, nullptr);

@@ -25,7 +25,17 @@
 // Tensor memory holds two buffers of {D: 128 cols, A_hi: 64 cols, A_lo: 64 cols},
 // so loading tile i+1, the MMAs of tile i and the stores of tile i-1 overlap.
 // Lanes of a warp always take 32 consecutive slices, so every global load and store
-// instruction walks consecutive addresses along the lowest non-target qubits.
+// instruction walks consecutive addresses along the lowest non-target qubits; with
+// the lowest target on bit 0 or 1 the stores are 16 bytes wide (see the epilogue).
+//
+// Variants (template parameters):
+//   kStaged: loads and stores walk the tile in memory order through a swizzled stage
+//            (for passes with 4 or more targets below bit 5);
+//   kTf32:   a TF32 hi/lo split in the complex block form, Re y = Xr Ur^T - Xi Ui^T and
+//            Im y = Xr Ui^T + Xi Ur^T: 48 MMAs of M = N = 128, K = 8 per tile, B images
+//            [Ur; Ui] and [-Ui; Ur] as windows of one [-Ui; Ur; Ui] image per split;
+//   kSub:    the input comes from a compact sub-state (the state is |0> on the qubits
+//            outside it), so the pass also expands that sub-state into the full state.
 //
 // Every wait is bounded (about one second of SM clock); on expiry the kernel raises
 // an error bit, drains its own MMAs and copies, frees its tensor memory and returns.
