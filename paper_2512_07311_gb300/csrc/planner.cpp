@@ -244,7 +244,7 @@ std::vector<Block> blocking(const Dag &d, size_t G, int k_max, int window, bool 
 // host threads, each state writing its own slot, and the merge walks the slots in
 // order, so the result does not depend on thread timing.
 std::vector<Block> beam_blocking(const Dag &d, size_t G, int k_max, int window, int width, int expand,
-                                 const std::vector<size_t> &head0, size_t placed0) {
+                                 const std::vector<size_t> &head0, size_t placed0, unsigned max_threads = 16) {
     struct Node {
         int parent;
         std::vector<int> gates;  // the block that led here
@@ -262,7 +262,7 @@ std::vector<Block> beam_blocking(const Dag &d, size_t G, int k_max, int window, 
     };
     std::vector<std::vector<Node>> steps;
     std::vector<State> states{State{head0, placed0, -1}};
-    const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    const unsigned hw = std::max(1u, std::min(max_threads, std::thread::hardware_concurrency()));
     while (true) {
         for (const State &st : states)
             if (st.placed == G) {
@@ -337,6 +337,8 @@ std::vector<Block> beam_blocking(const Dag &d, size_t G, int k_max, int window, 
 
 constexpr int kBeamWidth = 32;  // states kept per step of the beam search
 constexpr int kBeamExpand = 8;  // blocks grown per state and step
+constexpr int kSmallBeamWidth = 8;  // the beam that ranks the staged candidates
+constexpr int kSmallBeamExpand = 4;
 
 namespace {
 
@@ -402,8 +404,8 @@ double zero_cost(const Dag &d, const std::vector<Block> &b, int n, int span) {
 // stage of k = 2..5 excluded qubits, or two nested stages (k1 then k2 < k1 excluded),
 // the excluded qubits are chosen greedily to keep the largest closure (the gates that
 // precede every gate on them). Each stage's closure is blocked inside its sub-state,
-// and the rest of the circuit after it (greedily to pick the candidate, then by beam
-// search). On the 34-qubit 20-cycle workload at k = 6 this takes the full-state passes
+// and the rest of the circuit after it (by a small beam search to pick the candidate,
+// then by the full one). On the 34-qubit 20-cycle workload at k = 6 this takes the full-state passes
 // from 37 (45 passes, 8 of them on a 30-qubit sub-state) to 27.
 Blocking plan_blocks(int n, const std::vector<HostGate> &gates, int k_max, bool from_zero) {
     const size_t G = gates.size();
@@ -472,9 +474,10 @@ Blocking plan_blocks(int n, const std::vector<HostGate> &gates, int k_max, bool 
             c.X.push_back(X);
             pool = X;
         }
-        std::vector<size_t> h = c.head;
-        size_t pl = c.placed;
-        const std::vector<Block> rest = blocking_from(d, G, k_max, 2, true, ~0ull, h, pl);
+        // the rest estimated by a small single-threaded beam (greedy growth alone cannot tell
+        // the candidates apart: on the 34-qubit workload it gives 30 for all, the beam 28-34)
+        const std::vector<Block> rest =
+            beam_blocking(d, G, k_max, 0, kSmallBeamWidth, kSmallBeamExpand, c.head, c.placed, 1);
         c.sub_cost = sub_cost;
         c.est = double(rest.size()) + sub_cost;
         cands[task - nport] = std::move(c);
@@ -560,11 +563,12 @@ void plan_fuse(int n, const std::vector<HostGate> &gates, int k_max, int pad_to,
     make_passes(n, gates, plan_blocks(n, gates, k_max, false), pad_to, out);
 }
 
-// Up to five qubits that share no block are placed on bits 0..4, chosen greedily
-// from the qubits in the fewest blocks (lowest index on ties), by swapping places
-// with the qubits that sat there. The state kernels give a warp 32
-// neighbouring slices, which are side by side in memory only while the lowest
-// bits are not targets; with this layout a pass targets at most one of bits 0..4.
+// Five qubits are placed on bits 0..4, each swapping places with the qubit that sat
+// there: five that share no block (fewest memberships), else the five of the 16 least
+// used that the fewest blocks target twice or more. The state kernels give a warp 32 neighbouring
+// slices, which are side by side in memory only while the lowest bits are not targets;
+// with this layout a pass targets as few of bits 0..4 as the blocking allows (at most
+// one on the benchmark workloads).
 bool choose_layout(int n, const std::vector<HostGate> &gates, const Blocking &b, int *phys_of) {
     for (int q = 0; q < n; ++q) phys_of[q] = q;
     if (n < 12) return false;
@@ -581,20 +585,65 @@ bool choose_layout(int n, const std::vector<HostGate> &gates, const Blocking &b,
     std::vector<int> order(n);
     for (int q = 0; q < n; ++q) order[q] = q;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return count[x] < count[y]; });
+    // Five qubits that share no block, with the fewest memberships: a depth-first search
+    // over the qubits in membership order, pruned by the count so far. If no such five
+    // exist, the five of the 16 least-used qubits that the fewest blocks target twice or
+    // more (then the fewest memberships; every subset tried, at most C(16, 5) = 4368).
+    const int want = std::min(5, n);
+    std::vector<uint64_t> share(size_t(n), 0);  // qubits that share a block with q
+    for (uint64_t m : masks)
+        for (uint64_t r = m; r; r &= r - 1) share[size_t(std::countr_zero(r))] |= m;
     uint64_t chosen = 0;
-    int picked = 0;
-    for (int q : order) {
-        if (picked == 5) break;
-        bool clash = false;
-        for (uint64_t m : masks)
-            if (((m >> q) & 1) && (m & chosen)) {
-                clash = true;
-                break;
+    long best_cnt = -1;
+    {
+        uint64_t S = 0;
+        auto dfs = [&](auto &&self, int from, int left, long cnt) -> void {
+            if (left == 0) {
+                if (best_cnt < 0 || cnt < best_cnt) {
+                    best_cnt = cnt;
+                    chosen = S;
+                }
+                return;
             }
-        if (clash) continue;
-        chosen |= 1ull << q;
-        ++picked;
+            for (int i = from; i <= n - left; ++i) {
+                const int q = order[size_t(i)];
+                // order is by count: the cheapest completion adds left x count[q]
+                if (best_cnt >= 0 && cnt + long(left) * count[size_t(q)] >= best_cnt) return;
+                if (share[size_t(q)] & S) continue;
+                S |= 1ull << q;
+                self(self, i + 1, left - 1, cnt + count[size_t(q)]);
+                S &= ~(1ull << q);
+            }
+        };
+        dfs(dfs, 0, want, 0);
     }
+    if (best_cnt < 0) {
+        const int pool = std::min(n, 16);
+        long best_conf = -1;
+        std::vector<int> idx(static_cast<size_t>(want));
+        for (int i = 0; i < want; ++i) idx[size_t(i)] = i;
+        while (true) {
+            uint64_t S = 0;
+            long cnt = 0;
+            for (int i : idx) {
+                S |= 1ull << order[size_t(i)];
+                cnt += count[size_t(order[size_t(i)])];
+            }
+            long conf = 0;
+            for (uint64_t m : masks) conf += std::max(0, std::popcount(m & S) - 1);
+            if (best_conf < 0 || conf < best_conf || (conf == best_conf && cnt < best_cnt)) {
+                best_conf = conf;
+                best_cnt = cnt;
+                chosen = S;
+            }
+            int k = want - 1;  // next subset in lexicographic order
+            while (k >= 0 && idx[size_t(k)] == pool - want + k) --k;
+            if (k < 0) break;
+            ++idx[size_t(k)];
+            for (int r = k + 1; r < want; ++r) idx[size_t(r)] = idx[size_t(r - 1)] + 1;
+        }
+    }
+    const int picked = std::popcount(chosen);
     // pair the chosen qubits above bit `picked-1` with the unchosen qubits below it: at most
     // five transpositions, so restoring the identity layout takes at most five swaps
     std::vector<int> up, down;
