@@ -97,21 +97,20 @@ __global__ void __launch_bounds__(256) k_block_sums_map(const float2 *__restrict
         base |= uint64_t(lane) << 1;
         uint64_t s0 = 0, s1 = 0, off = 0;
         auto next = [&](uint64_t o) { return ((o | ~inner) + 1ull) & inner; };  // masked increment
-        do {  // every value of the inner bits in increasing order, four loads in flight
+        do {  // every value of the inner bits in increasing order, eight loads in flight
             // (the count 2^popcount(inner) is a power of two >= 16: P has 10 bits, at most 6 of
             // them among bits 0..5)
-            const uint64_t o1 = next(off), o2 = next(o1), o3 = next(o2);
-            float4 v[4];
-            v[0] = __ldg(reinterpret_cast<const float4 *>(psi + (base | off)));
-            v[1] = __ldg(reinterpret_cast<const float4 *>(psi + (base | o1)));
-            v[2] = __ldg(reinterpret_cast<const float4 *>(psi + (base | o2)));
-            v[3] = __ldg(reinterpret_cast<const float4 *>(psi + (base | o3)));
+            float4 v[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < 8; ++u) {
+                v[u] = __ldg(reinterpret_cast<const float4 *>(psi + (base | off)));
+                off = next(off);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
                 s0 += fx_sq(v[u].x, bad) + fx_sq(v[u].y, bad);
                 s1 += fx_sq(v[u].z, bad) + fx_sq(v[u].w, bad);
             }
-            off = next(o3);
         } while (off != 0);
         if (b0p) s0 += s1;
 #pragma unroll
