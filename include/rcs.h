@@ -250,6 +250,27 @@ int rcs_sample(rcs_ctx *ctx, uint64_t shots, uint64_t seed, uint64_t *out_bits);
 /* As rcs_sample, writing to DEVICE memory d_out_bits; asynchronous. */
 int rcs_sample_device(rcs_ctx *ctx, uint64_t shots, uint64_t seed, uint64_t *d_out_bits);
 
+/* Shots first_shot .. first_shot + shots - 1 of the same stream (shot s always uses
+ * uniform u_s): sampling a state in pieces, in one process or in several that loaded
+ * the same saved state, gives exactly the draws of one rcs_sample call. HOST out_bits.
+ * Synchronous. RCS_ERR_ARG if the range overflows 64 bits. */
+int rcs_sample_range(rcs_ctx *ctx, uint64_t first_shot, uint64_t shots, uint64_t seed, uint64_t *out_bits);
+
+/* ------------------------------------------------------------------ persistence (Section 3.2 items 2-3)
+
+ * The paper writes the built state to a shared filesystem and reloads it in many
+ * sampling jobs. rcs_state_save writes the context's state to `path`: a 280-byte
+ * header (magic "RCSSTATE", version 1, n, the stored layout of each qubit, 2^n),
+ * then 2^n complex64 amplitudes in stored order (8 x 2^n bytes; 128 GiB at 34
+ * qubits), streamed through a 64 MiB pinned buffer. rcs_state_load reads such a file
+ * into a context of the same qubit count, layout included, so samples, amplitudes
+ * and XEB stay in the circuit's own numbering. Both synchronous. Errors: RCS_ERR_ARG
+ * for a file that cannot be opened, written or read in full, a wrong header or qubit
+ * count (the state is untouched when the header is rejected; a truncated file
+ * leaves it undefined), RCS_ERR_OOM / RCS_ERR_CUDA for the staging copies. */
+int rcs_state_save(rcs_ctx *ctx, const char *path);
+int rcs_state_load(rcs_ctx *ctx, const char *path);
+
 /* ------------------------------------------------------------------ scoring (Section 3.2 item 4) */
 
 /* Linear XEB of the samples against the current state:

@@ -85,6 +85,9 @@ SIGNATURES = [
     ("rcs_norm", ctypes.c_int, [_P, _f64p]),
     ("rcs_sample", ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint64, _u64p]),
     ("rcs_sample_device", ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p]),
+    ("rcs_sample_range", ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, _u64p]),
+    ("rcs_state_save", ctypes.c_int, [_P, ctypes.c_char_p]),
+    ("rcs_state_load", ctypes.c_int, [_P, ctypes.c_char_p]),
     ("rcs_xeb", ctypes.c_int, [_P, _u64p, ctypes.c_size_t, _f64p]),
     ("rcs_xeb_device", ctypes.c_int, [_P, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     ("rcs_batch_create", ctypes.c_int, [ctypes.POINTER(rcs_batch_item), ctypes.c_size_t, ctypes.POINTER(rcs_opts),
@@ -297,6 +300,20 @@ def rcs_sample(ctx, shots: int, seed: int) -> np.ndarray:
     out = np.zeros(shots, dtype=np.uint64)
     _check(load().rcs_sample(ctx, shots, seed, out.ctypes.data_as(_u64p)), ctx)
     return out
+
+
+def rcs_sample_range(ctx, first_shot: int, shots: int, seed: int) -> np.ndarray:
+    out = np.zeros(shots, dtype=np.uint64)
+    _check(load().rcs_sample_range(ctx, first_shot, shots, seed, out.ctypes.data_as(_u64p)), ctx)
+    return out
+
+
+def rcs_state_save(ctx, path: str):
+    _check(load().rcs_state_save(ctx, os.fsencode(path)), ctx)
+
+
+def rcs_state_load(ctx, path: str):
+    _check(load().rcs_state_load(ctx, os.fsencode(path)), ctx)
 
 
 def rcs_sample_device(ctx, shots: int, seed: int, d_out: int):

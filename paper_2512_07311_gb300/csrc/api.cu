@@ -921,6 +921,111 @@ int rcs_state_write(rcs_ctx *c, uint64_t first, uint64_t count, const float *in_
     return drain_errors(c);
 }
 
+namespace {
+// File form of a saved state: this header, then the 2^n stored amplitudes (complex64,
+// interleaved, little-endian) in stored order.
+struct StateFileHeader {
+    char magic[8];       // "RCSSTATE"
+    uint32_t version;    // 1
+    int32_t n;
+    int32_t phys_of[64];  // stored bit of each circuit qubit (the layout)
+    uint64_t amplitudes;  // 2^n
+};
+static_assert(sizeof(StateFileHeader) == 280, "state file header layout");
+constexpr size_t kIoChunk = size_t(64) << 20;  // bytes per copy through the pinned buffer
+
+struct PinnedBuffer {
+    void *p = nullptr;
+    ~PinnedBuffer() {
+        if (p) cudaFreeHost(p);
+    }
+};
+}  // namespace
+
+int rcs_state_save(rcs_ctx *c, const char *path) {
+    if (!c || !path) return fail(c, RCS_ERR_ARG, "null argument");
+    RCS_TRY(c)
+    if (int rc = materialize(c); rc != RCS_OK) return rc;
+    StateFileHeader h{};
+    std::memcpy(h.magic, "RCSSTATE", 8);
+    h.version = 1;
+    h.n = c->n;
+    for (int q = 0; q < 64; ++q) h.phys_of[q] = q < c->n ? c->phys_of[q] : q;
+    h.amplitudes = uint64_t(1) << c->n;
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(c, RCS_ERR_ARG, std::string("cannot open for writing: ") + path);
+    PinnedBuffer buf;
+    const size_t total = size_t(8) << c->n;
+    const size_t chunk = std::min(total, kIoChunk);
+    int rc = RCS_OK;
+    if (std::fwrite(&h, sizeof(h), 1, f) != 1) rc = fail(c, RCS_ERR_ARG, "short write of the state header");
+    if (rc == RCS_OK && cudaHostAlloc(&buf.p, chunk, cudaHostAllocDefault) != cudaSuccess)
+        rc = fail(c, RCS_ERR_OOM, "pinned staging buffer");
+    for (size_t off = 0; rc == RCS_OK && off < total; off += chunk) {
+        const size_t len = std::min(chunk, total - off);
+        if (cudaMemcpyAsync(buf.p, reinterpret_cast<const uint8_t *>(c->psi) + off, len, cudaMemcpyDeviceToHost,
+                            c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)
+            rc = fail(c, RCS_ERR_CUDA, "state download");
+        else if (std::fwrite(buf.p, 1, len, f) != len)
+            rc = fail(c, RCS_ERR_ARG, std::string("short write: ") + path);
+    }
+    if (std::fclose(f) != 0 && rc == RCS_OK) rc = fail(c, RCS_ERR_ARG, std::string("close failed: ") + path);
+    if (rc != RCS_OK) return rc;
+    return drain_errors(c);
+    RCS_CATCH(c)
+}
+
+int rcs_state_load(rcs_ctx *c, const char *path) {
+    if (!c || !path) return fail(c, RCS_ERR_ARG, "null argument");
+    RCS_TRY(c)
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(c, RCS_ERR_ARG, std::string("cannot open: ") + path);
+    StateFileHeader h{};
+    int rc = RCS_OK;
+    if (std::fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, "RCSSTATE", 8) != 0 || h.version != 1)
+        rc = fail(c, RCS_ERR_ARG, std::string("not a saved state (version 1): ") + path);
+    else if (h.n != c->n || h.amplitudes != (uint64_t(1) << c->n))
+        rc = fail(c, RCS_ERR_ARG, "the saved state has " + std::to_string(h.n) + " qubits, the context " +
+                                      std::to_string(c->n));
+    if (rc == RCS_OK) {  // the layout must be a permutation of 0..n-1
+        uint64_t seen = 0;
+        for (int q = 0; q < c->n; ++q) {
+            const int p = h.phys_of[q];
+            if (p < 0 || p >= c->n || ((seen >> p) & 1)) {
+                rc = fail(c, RCS_ERR_ARG, "corrupt layout in the state header");
+                break;
+            }
+            seen |= 1ull << p;
+        }
+    }
+    PinnedBuffer buf;
+    const size_t total = size_t(8) << c->n;
+    const size_t chunk = std::min(total, kIoChunk);
+    if (rc == RCS_OK && cudaHostAlloc(&buf.p, chunk, cudaHostAllocDefault) != cudaSuccess)
+        rc = fail(c, RCS_ERR_OOM, "pinned staging buffer");
+    if (rc == RCS_OK) {  // the state is being replaced: anything pending on it is dropped
+        c->zero_pending = false;
+        c->fresh = false;
+        c->sums_valid = false;
+    }
+    for (size_t off = 0; rc == RCS_OK && off < total; off += chunk) {
+        const size_t len = std::min(chunk, total - off);
+        if (std::fread(buf.p, 1, len, f) != len) {
+            rc = fail(c, RCS_ERR_ARG, std::string("truncated state file: ") + path);
+        } else if (cudaMemcpyAsync(reinterpret_cast<uint8_t *>(c->psi) + off, buf.p, len, cudaMemcpyHostToDevice,
+                                   c->stream) != cudaSuccess ||
+                   cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            rc = fail(c, RCS_ERR_CUDA, "state upload");
+        }
+    }
+    std::fclose(f);
+    if (rc != RCS_OK) return rc;
+    for (int q = 0; q < c->n; ++q) c->phys_of[q] = h.phys_of[q];
+    return drain_errors(c);
+    RCS_CATCH(c)
+}
+
 int rcs_state_device(rcs_ctx *c, void **d_state) {
     if (!c || !d_state) return fail(c, RCS_ERR_ARG, "null argument");
     if (int rc = materialize(c); rc != RCS_OK) return rc;
@@ -953,9 +1058,28 @@ int rcs_sample_device(rcs_ctx *c, uint64_t shots, uint64_t seed, uint64_t *d_out
     if (!d_out_bits) return fail(c, RCS_ERR_ARG, "null output");
     int rc = ensure_sums(c);
     if (rc != RCS_OK) return rc;
-    if (launch_sample(c->psi, c->n, c->bsum, c->bpre, c->total, shots, seed, d_out_bits, to_stored(c), c->stream) !=
-        RCS_OK)
+    if (launch_sample(c->psi, c->n, c->bsum, c->bpre, c->total, 0, shots, seed, d_out_bits, to_stored(c),
+                      c->stream) != RCS_OK)
         return fail(c, RCS_ERR_CUDA, "sampler launch: " + take_launch_error());
+    return RCS_OK;
+}
+
+int rcs_sample_range(rcs_ctx *c, uint64_t first_shot, uint64_t shots, uint64_t seed, uint64_t *out_bits) {
+    if (!c) return fail(nullptr, RCS_ERR_ARG, "null context");
+    if (shots == 0) return RCS_OK;
+    if (!out_bits) return fail(c, RCS_ERR_ARG, "null output");
+    if (first_shot > ~0ull - shots) return fail(c, RCS_ERR_ARG, "shot range overflows");
+    int rc = ensure_sums(c);
+    if (rc != RCS_OK) return rc;
+    if ((rc = ensure_u64(c, size_t(shots))) != RCS_OK) return rc;
+    if (launch_sample(c->psi, c->n, c->bsum, c->bpre, c->total, first_shot, shots, seed, c->d_u64, to_stored(c),
+                      c->stream) != RCS_OK)
+        return fail(c, RCS_ERR_CUDA, "sampler launch: " + take_launch_error());
+    RCS_CUDA(c, cudaMemcpyAsync(out_bits, c->d_u64, shots * 8, cudaMemcpyDeviceToHost, c->stream), "download samples");
+    if ((rc = drain_errors(c)) != RCS_OK) {
+        c->sums_valid = false;
+        return rc;
+    }
     return RCS_OK;
 }
 

@@ -474,7 +474,7 @@ int launch_sampling(rcs_batch *b, InstHost &h, cudaStream_t st) {
     int rc;
     if ((rc = launch_block_sums(h.psi, h.n, h.bsum, b->d_err, plan_to_stored(h.plan), st)) != RCS_OK ||
         (rc = launch_block_scan(h.bsum, h.bpre, h.chunk, h.total, h.n, b->d_err, st)) != RCS_OK ||
-        (rc = launch_sample(h.psi, h.n, h.bsum, h.bpre, h.total, h.shots, h.seed, h.d_bits, plan_to_stored(h.plan),
+        (rc = launch_sample(h.psi, h.n, h.bsum, h.bpre, h.total, 0, h.shots, h.seed, h.d_bits, plan_to_stored(h.plan),
                             st)) != RCS_OK ||
         (rc = launch_xeb(h.psi, h.n, h.d_bits, h.shots, h.total, h.d_xeb + 1, h.d_xeb, plan_to_stored(h.plan), st)) !=
             RCS_OK)

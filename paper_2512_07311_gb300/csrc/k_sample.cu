@@ -288,7 +288,8 @@ __device__ __forceinline__ bool above(uint64_t a, uint64_t rhi, uint64_t rlo) {
 __global__ void __launch_bounds__(256) k_sample(const float2 *__restrict__ psi, int blog2, uint64_t nblocks,
                                                  const uint64_t *__restrict__ bsum,
                                                  const uint64_t *__restrict__ bpre,
-                                                 const uint64_t *__restrict__ total, uint64_t shots, uint64_t seed,
+                                                 const uint64_t *__restrict__ total, uint64_t first, uint64_t shots,
+                                                 uint64_t seed,
                                                  uint64_t *__restrict__ out, const BitMap smap) {
     const int lane = threadIdx.x & 31;
     const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
@@ -314,7 +315,8 @@ __global__ void __launch_bounds__(256) k_sample(const float2 *__restrict__ psi, 
             if (lane == 0) out[s] = ~0ull;
             continue;
         }
-        const uint64_t m = philox_word(s >> 2, seed, int(s & 3)) >> 11;  // u = m * 2^-53
+        const uint64_t g = first + s;  // index of the shot in the stream of this seed
+        const uint64_t m = philox_word(g >> 2, seed, int(g & 3)) >> 11;  // u = m * 2^-53
         const uint64_t rlo = m * T, rhi = __umul64hi(m, T);
         // smallest block whose inclusive prefix crosses the target
         uint64_t lo = 0, hi = nblocks - 1;
@@ -389,14 +391,15 @@ BitMap identity_map(int n) {
 }
 
 int launch_sample(const void *psi, int n, const uint64_t *bsum, const uint64_t *bpre, const uint64_t *total,
-                  uint64_t shots, uint64_t seed, uint64_t *d_out, const BitMap &to_stored, void *stream) {
+                  uint64_t first, uint64_t shots, uint64_t seed, uint64_t *d_out, const BitMap &to_stored,
+                  void *stream) {
     if (shots == 0) return RCS_OK;
     const int bl = block_log2(n);
     if (!to_stored.identity && bl < 10) return RCS_ERR_UNSUPPORTED;
     const uint64_t nblocks = 1ull << (n - bl);
     const unsigned grid = grid_for(shots * 32, 256, device_sm_count(), 8);
     k_sample<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<const float2 *>(psi), bl, nblocks, bsum,
-                                                                  bpre, total, shots, seed, d_out, to_stored);
+                                                                  bpre, total, first, shots, seed, d_out, to_stored);
     return launch_status(__func__);
 }
 
