@@ -13,6 +13,11 @@
 #include <cmath>
 #include <cstring>
 #include <array>
+#include <mutex>
+#include <memory>
+#include <functional>
+#include <condition_variable>
+#include <atomic>
 #include <map>
 #include <thread>
 
@@ -61,22 +66,86 @@ static void left_multiply(std::vector<cd> &U, int k, const HostGate &g, const in
     }
 }
 
-// Runs f(0 .. count-1) on up to 16 host threads (each index once; f must only write
-// its own slot).
+// A persistent pool of host threads (up to 15 workers, started on first use). A job is a
+// range of indices; the calling thread works on its own job as well, so nested jobs (a
+// beam search inside a task) always make progress even when every worker is busy.
+class TaskPool {
+  public:
+    static TaskPool &get() {
+        static TaskPool *pool = new TaskPool;  // never destroyed: workers sleep until exit
+        return *pool;
+    }
+    void run(size_t count, const std::function<void(size_t)> &f) {
+        if (count == 0) return;
+        auto job = std::make_shared<Job>(f, count);
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            jobs_.push_back(job);
+        }
+        cv_.notify_all();
+        work_on(*job);
+        std::unique_lock<std::mutex> lk(mu_);
+        done_cv_.wait(lk, [&] { return job->done.load() == count; });
+        jobs_.erase(std::find(jobs_.begin(), jobs_.end(), job));
+    }
+    size_t workers() const { return threads_; }
+
+  private:
+    struct Job {
+        Job(const std::function<void(size_t)> &fn, size_t c) : f(fn), count(c) {}
+        std::function<void(size_t)> f;
+        size_t count;
+        std::atomic<size_t> next{0}, done{0};
+    };
+    TaskPool() {
+        threads_ = std::min<size_t>(15, std::max(1u, std::thread::hardware_concurrency()) - 1);
+        for (size_t t = 0; t < threads_; ++t) std::thread([this] { worker(); }).detach();
+    }
+    void work_on(Job &j) {
+        for (;;) {
+            const size_t i = j.next.fetch_add(1);
+            if (i >= j.count) return;
+            j.f(i);
+            if (j.done.fetch_add(1) + 1 == j.count) {
+                std::lock_guard<std::mutex> lk(mu_);
+                done_cv_.notify_all();
+            }
+        }
+    }
+    void worker() {
+        for (;;) {
+            std::shared_ptr<Job> j;
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [&] {
+                    for (const auto &x : jobs_)
+                        if (x->next.load() < x->count) return true;
+                    return false;
+                });
+                for (const auto &x : jobs_)
+                    if (x->next.load() < x->count) {
+                        j = x;
+                        break;
+                    }
+            }
+            if (j) work_on(*j);
+        }
+    }
+    std::mutex mu_;
+    std::condition_variable cv_, done_cv_;
+    std::vector<std::shared_ptr<Job>> jobs_;
+    size_t threads_ = 0;
+};
+
+// Runs f(0 .. count-1) on the task pool (each index once; f must only write its own
+// slot), or inline when there is no parallelism to gain.
 template <class F>
 static void parallel_for(size_t count, F f) {
-    const size_t nt = std::min<size_t>(count, std::max(1u, std::min(16u, std::thread::hardware_concurrency())));
-    if (nt <= 1) {
+    if (count <= 1 || TaskPool::get().workers() == 0) {
         for (size_t i = 0; i < count; ++i) f(i);
         return;
     }
-    std::vector<std::thread> pool;
-    pool.reserve(nt);
-    for (size_t t = 0; t < nt; ++t)
-        pool.emplace_back([&, t] {
-            for (size_t i = t; i < count; i += nt) f(i);
-        });
-    for (std::thread &th : pool) th.join();
+    TaskPool::get().run(count, std::function<void(size_t)>(f));
 }
 
 static Pass make_pass(PassKind kind, uint64_t qmask, const std::vector<const HostGate *> &blk) {
@@ -262,7 +331,6 @@ std::vector<Block> beam_blocking(const Dag &d, size_t G, int k_max, int window, 
     };
     std::vector<std::vector<Node>> steps;
     std::vector<State> states{State{head0, placed0, -1}};
-    const unsigned hw = std::max(1u, std::min(max_threads, std::thread::hardware_concurrency()));
     while (true) {
         for (const State &st : states)
             if (st.placed == G) {
@@ -294,16 +362,10 @@ std::vector<Block> beam_blocking(const Dag &d, size_t G, int k_max, int window, 
             if (cs.size() > size_t(expand)) cs.resize(size_t(expand));
             slot[i] = std::move(cs);
         };
-        const size_t nt = std::min<size_t>(hw, states.size());
-        if (nt <= 1) {
+        if (max_threads <= 1) {
             for (size_t i = 0; i < states.size(); ++i) work(i);
         } else {
-            std::vector<std::thread> pool;
-            for (size_t t = 0; t < nt; ++t)
-                pool.emplace_back([&, t] {
-                    for (size_t i = t; i < states.size(); i += nt) work(i);
-                });
-            for (std::thread &th : pool) th.join();
+            parallel_for(states.size(), work);
         }
         // merge equal frontiers (first occurrence in state order wins ties), keep the best `width`
         std::map<std::vector<size_t>, std::pair<size_t, size_t>> seen;  // head -> (slot, index)
