@@ -391,11 +391,12 @@ def main():
     t_pass_s = statistics.median(pass_ms) / 1e3 / full_passes
     # launches per step: sub-state reset, expansions between sub-states, the final expansion
     # unless the first full pass reads the last sub-state, every pass, block sums, the 3-phase
-    # scan, the sampler and the 2-phase XEB
+    # scan, the sampler (locate, 3-phase scan of its per-block counts, order, resolve) and the
+    # 2-phase XEB
     stages = int(info["prefix_stages"])
     fused = prefix > 0 and full_passes == passes - prefix - 1
     setup = 1 + max(stages - 1, 0) + (0 if (prefix == 0 or fused) else 1)
-    gpu_launches = passes + setup + 1 + 3 + 1 + 2
+    gpu_launches = passes + setup + 1 + 3 + 6 + 2
     bytes_per_launch = 16.0 * 2.0**n
     achieved = bytes_per_launch / t_pass_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",

@@ -244,10 +244,13 @@ int rcs_norm(rcs_ctx *ctx, double *out);
  * word (s mod 4) of Philox4x64-10(counter = (s div 4, 0, 0, 0), key = (seed, 0))
  * mapped to [0,1) as (x >> 11) 2^-53. Zero-probability indices are never drawn.
  * Writes shots uint64 indices to HOST out_bits. Synchronous. The state must
- * have norm < 3.9 (unitary circuits keep it at 1). */
+ * have norm < 3.9 (unitary circuits keep it at 1); a state of norm 0 gives
+ * 2^64 - 1 for every shot. */
 int rcs_sample(rcs_ctx *ctx, uint64_t shots, uint64_t seed, uint64_t *out_bits);
 
-/* As rcs_sample, writing to DEVICE memory d_out_bits; asynchronous. */
+/* As rcs_sample, writing to DEVICE memory d_out_bits; asynchronous (a call with
+ * more shots than any before it on this context first grows a device scratch of
+ * 8 bytes per shot, which synchronizes the context's stream). */
 int rcs_sample_device(rcs_ctx *ctx, uint64_t shots, uint64_t seed, uint64_t *d_out_bits);
 
 /* Shots first_shot .. first_shot + shots - 1 of the same stream (shot s always uses

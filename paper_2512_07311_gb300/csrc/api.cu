@@ -30,6 +30,8 @@ struct rcs_ctx {
     size_t u64_cap = 0;
     double *d_f64 = nullptr;
     size_t f64_cap = 0;
+    uint64_t *d_order = nullptr;  // the sampler's shots grouped by block
+    size_t order_cap = 0;
     uint8_t *d_ops = nullptr;  // tensor-core operand images of rcs_apply_circuit plans
     size_t ops_cap = 0;
     // Qubit layout: circuit qubit q is stored at index bit phys_of[q]. A fresh state
@@ -85,6 +87,18 @@ int ensure_u64(rcs_ctx *c, size_t count) {
     size_t cap = std::max<size_t>(count, 1024);
     RCS_CUDA(c, cudaMalloc(&c->d_u64, cap * sizeof(uint64_t)), "cudaMalloc scratch");
     c->u64_cap = cap;
+    return RCS_OK;
+}
+
+int ensure_order(rcs_ctx *c, size_t count) {
+    if (count <= c->order_cap) return RCS_OK;
+    RCS_CUDA(c, cudaStreamSynchronize(c->stream), "stream sync");
+    if (c->d_order) cudaFree(c->d_order);
+    c->d_order = nullptr;
+    c->order_cap = 0;
+    size_t cap = std::max<size_t>(count, 1024);
+    RCS_CUDA(c, cudaMalloc(&c->d_order, cap * sizeof(uint64_t)), "cudaMalloc sampler scratch");
+    c->order_cap = cap;
     return RCS_OK;
 }
 
@@ -528,6 +542,7 @@ void rcs_destroy(rcs_ctx *c) {
     cudaFree(c->d_err);
     cudaFree(c->d_u64);
     cudaFree(c->d_f64);
+    cudaFree(c->d_order);
     cudaFree(c->d_ops);
     cudaFree(c->d_sub);
     if (c->ev_full[0]) cudaEventDestroy(c->ev_full[0]);
@@ -1058,8 +1073,10 @@ int rcs_sample_device(rcs_ctx *c, uint64_t shots, uint64_t seed, uint64_t *d_out
     if (!d_out_bits) return fail(c, RCS_ERR_ARG, "null output");
     int rc = ensure_sums(c);
     if (rc != RCS_OK) return rc;
-    if (launch_sample(c->psi, c->n, c->bsum, c->bpre, c->total, 0, shots, seed, d_out_bits, to_stored(c),
-                      c->stream) != RCS_OK)
+    if ((rc = ensure_order(c, size_t(shots))) != RCS_OK) return rc;
+    // the block sums are spent as the sampler's per-block counts (the prefix and T stay)
+    if (launch_sample(c->psi, c->n, c->bsum, c->bpre, c->total, c->chunk, 0, shots, seed, d_out_bits, c->d_order,
+                      c->d_err, to_stored(c), c->stream) != RCS_OK)
         return fail(c, RCS_ERR_CUDA, "sampler launch: " + take_launch_error());
     return RCS_OK;
 }
@@ -1071,9 +1088,9 @@ int rcs_sample_range(rcs_ctx *c, uint64_t first_shot, uint64_t shots, uint64_t s
     if (first_shot > ~0ull - shots) return fail(c, RCS_ERR_ARG, "shot range overflows");
     int rc = ensure_sums(c);
     if (rc != RCS_OK) return rc;
-    if ((rc = ensure_u64(c, size_t(shots))) != RCS_OK) return rc;
-    if (launch_sample(c->psi, c->n, c->bsum, c->bpre, c->total, first_shot, shots, seed, c->d_u64, to_stored(c),
-                      c->stream) != RCS_OK)
+    if ((rc = ensure_u64(c, size_t(shots))) != RCS_OK || (rc = ensure_order(c, size_t(shots))) != RCS_OK) return rc;
+    if (launch_sample(c->psi, c->n, c->bsum, c->bpre, c->total, c->chunk, first_shot, shots, seed, c->d_u64,
+                      c->d_order, c->d_err, to_stored(c), c->stream) != RCS_OK)
         return fail(c, RCS_ERR_CUDA, "sampler launch: " + take_launch_error());
     RCS_CUDA(c, cudaMemcpyAsync(out_bits, c->d_u64, shots * 8, cudaMemcpyDeviceToHost, c->stream), "download samples");
     if ((rc = drain_errors(c)) != RCS_OK) {

@@ -214,6 +214,7 @@ struct InstHost {
     float2 *psi = nullptr;
     uint64_t *bsum = nullptr, *bpre = nullptr, *chunk = nullptr, *total = nullptr;
     uint64_t *d_bits = nullptr;  // shots
+    uint64_t *d_order = nullptr;  // shots: the sampler's scratch
     double *d_xeb = nullptr;     // result + partials
     uint64_t items_per_pass = 0;
 };
@@ -455,6 +456,7 @@ void free_batch(rcs_batch *b) {
         cudaFree(h.chunk);
         cudaFree(h.total);
         cudaFree(h.d_bits);
+        cudaFree(h.d_order);
         cudaFree(h.d_xeb);
         cudaFree(h.d_ops);
         cudaFree(h.d_sub);
@@ -474,8 +476,8 @@ int launch_sampling(rcs_batch *b, InstHost &h, cudaStream_t st) {
     int rc;
     if ((rc = launch_block_sums(h.psi, h.n, h.bsum, b->d_err, plan_to_stored(h.plan), st)) != RCS_OK ||
         (rc = launch_block_scan(h.bsum, h.bpre, h.chunk, h.total, h.n, b->d_err, st)) != RCS_OK ||
-        (rc = launch_sample(h.psi, h.n, h.bsum, h.bpre, h.total, 0, h.shots, h.seed, h.d_bits, plan_to_stored(h.plan),
-                            st)) != RCS_OK ||
+        (rc = launch_sample(h.psi, h.n, h.bsum, h.bpre, h.total, h.chunk, 0, h.shots, h.seed, h.d_bits, h.d_order,
+                            b->d_err, plan_to_stored(h.plan), st)) != RCS_OK ||
         (rc = launch_xeb(h.psi, h.n, h.d_bits, h.shots, h.total, h.d_xeb + 1, h.d_xeb, plan_to_stored(h.plan), st)) !=
             RCS_OK)
         return bfail(b, rc, "sampling launch: " + take_launch_error());
@@ -631,6 +633,7 @@ int rcs_batch_create(const rcs_batch_item *items, size_t n_items, const rcs_opts
             BCUDA(b, cudaMalloc(&h.chunk, (scan_chunks(h.n) + 1) * 8), "scan chunks");
             BCUDA(b, cudaMalloc(&h.total, 8), "total");
             BCUDA(b, cudaMalloc(&h.d_bits, std::max<uint64_t>(h.shots, 1) * 8), "samples");
+            BCUDA(b, cudaMalloc(&h.d_order, std::max<uint64_t>(h.shots, 1) * 8), "sampler scratch");
             BCUDA(b, cudaMalloc(&h.d_xeb, (1 + xeb_partials_count(std::max<uint64_t>(h.shots, 1))) * 8), "xeb");
         }
         BCUDA(b, cudaMalloc(&b->d_err, 8), "error word");

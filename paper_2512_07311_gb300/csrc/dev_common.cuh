@@ -21,32 +21,30 @@ __device__ __forceinline__ float2 cmac(float2 acc, float2 m, float2 a) {
     return acc;
 }
 
-// round(x^2 * 2^62) for finite |x| < 2, exactly (from the float's exponent and
-// 24-bit mantissa, one 32x32->64 multiply); sets bad for |x| >= 2, Inf or NaN.
-// Integer-only on purpose: on GB300 the 64-bit float-to-integer conversions of an
-// FP32 error-free split run at the FP64 rate and made the reduction 2.6x slower.
-__device__ __forceinline__ uint64_t fx_sq(float x, int &bad) {
-    const uint32_t b = __float_as_uint(x) & 0x7fffffffu;
-    uint32_t e = b >> 23;
-    uint32_t m = b & 0x7fffffu;
-    if (e) m |= 0x800000u;
-    else e = 1;
-    if (e >= 128u) bad = 1;
-    const int sh = 2 * int(e) - 238;  // x^2 * 2^62 = m^2 * 2^sh, m^2 < 2^48
-    if (sh <= -18) {
-        // r = -sh >= 18 (|x| < 2^-8, the usual case): the result is below 2^31, so
-        // floor(m^2 / 2^(r-1)) = floor(floor(m^2 / 2^16) / 2^(r-17)) in 32-bit integers,
-        // with floor(m^2 / 2^16) the high word of (m * 2^8)^2
-        const int r = -sh;
-        if (r > 48) return 0ull;
-        const uint32_t a = m << 8;
-        return uint64_t(((__umulhi(a, a) >> (r - 17)) + 1u) >> 1);  // round half up
-    }
-    const uint64_t m2 = uint64_t(m) * uint64_t(m);
-    if (sh >= 0) return sh <= 16 ? (m2 << sh) : 0ull;
-    const int r = -sh;
-    return ((m2 >> (r - 1)) + 1ull) >> 1;  // round half up
+// floor(x^2 * 2^62) for finite |x| < 2, exactly, in integer arithmetic only.
+// With the float's biased exponent e and 24-bit significand m (implicit bit set),
+// x = m * 2^(e - 150); with a = m * 2^8 (a 32-bit word whose top bit is the implicit
+// bit), x^2 * 2^62 = a^2 * 2^-(254 - 2e), so the value is a^2 (< 2^64) shifted right
+// by 254 - 2e. The shift clamps at 64 (PTX shr), which gives the exact 0 for zero
+// and subnormals (e = 0: shift 254) and for every |x| < 2^-31.
+// `seen` collects the raw bits: bit 30 of it is set once any input had |x| >= 2,
+// Inf or NaN (e >= 128), for which the value returned is 0.
+// Branch-free and 32-bit except one wide multiply and one 64-bit shift: on GB300 the
+// reduction over a 2^34-amplitude state stays bound by HBM, not by the integer pipe
+// (a two-path form that rounded to nearest ran the ALU pipe at 75% and HBM at 36%).
+__device__ __forceinline__ uint64_t fx_sq(float x, uint32_t &seen) {
+    const uint32_t u = __float_as_uint(x);
+    seen |= u;
+    const uint32_t a = (u << 8) | 0x80000000u;
+    const uint32_t k = 254u - ((u >> 22) & 0x1feu);  // 254 - 2e; wraps to a huge shift for e >= 128
+    const uint64_t t = uint64_t(a) * uint64_t(a);
+    uint64_t q;
+    asm("shr.b64 %0, %1, %2;" : "=l"(q) : "l"(t), "r"(k));
+    return q;
 }
+
+// True once fx_sq has seen an input it cannot represent (|x| >= 2, Inf, NaN).
+__device__ __forceinline__ bool fx_overflow(uint32_t seen) { return (seen & 0x40000000u) != 0; }
 
 // Applies a bit permutation of basis indices (see BitMap).
 template <class Map>

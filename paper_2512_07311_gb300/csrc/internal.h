@@ -162,9 +162,12 @@ int launch_block_scan(const uint64_t *bsum, uint64_t *bpre, uint64_t *chunk_tot,
 // draws the caller index x = min{i : C_i > u T} with C in the caller's order, from
 // block sums made with the same map.
 // Shots first .. first + shots - 1 of the seed's stream (shot g uses uniform g).
-int launch_sample(const void *psi, int n, const uint64_t *bsum, const uint64_t *bpre, const uint64_t *total,
-                  uint64_t first, uint64_t shots, uint64_t seed, uint64_t *d_out, const BitMap &to_stored,
-                  void *stream);
+// Needs the block prefix bpre and total T of launch_block_scan; hist (2^(n-10) entries,
+// the block sums' array: overwritten), chunk (scan_chunks(n) + 1 entries) and order
+// (shots entries) are scratch.
+int launch_sample(const void *psi, int n, uint64_t *hist, const uint64_t *bpre, const uint64_t *total, uint64_t *chunk,
+                  uint64_t first, uint64_t shots, uint64_t seed, uint64_t *d_out, uint64_t *order, int *d_err,
+                  const BitMap &to_stored, void *stream);
 int launch_gather(const void *psi, int n, const uint64_t *d_bits, size_t count, double *d_out_re_im, int *d_err,
                   const BitMap &in_map, void *stream);
 int launch_xeb(const void *psi, int n, const uint64_t *d_samples, size_t count, const uint64_t *total,

@@ -2,17 +2,21 @@
 // draw shots from |psi|^2, then score them with linear XEB).
 //
 // Probabilities enter every 2^n-term reduction as exact fixed-point integers:
-// q(x) = round(x^2 * 2^62) for each FP32 component x, computed from the float's
-// exponent and 24-bit mantissa with one 32x32->64 integer multiply. Sums of q are
-// exact (no rounding, any order), so the block sums, the block prefix scan, the
-// norm T and every cumulative probability C_i are exact multiples of 2^-62 that
-// do not depend on the summation order. GB300 runs FP64 at a small fraction of
+// q(x) = floor(x^2 * 2^62) for each FP32 component x, computed from the float's
+// exponent and 24-bit mantissa with one 32x32->64 integer multiply and one shift.
+// Sums of q are exact (no rounding, any order), so the block sums, the block prefix
+// scan, the norm T and every cumulative probability C_i are exact multiples of 2^-62
+// that do not depend on the summation order. GB300 runs FP64 at a small fraction of
 // its FP32/INT32 rate, so this keeps the reduction pass bound by HBM instead of by
-// the FP64 pipe, with a rounding error (2^-63 per term) far below FP64's.
+// the FP64 pipe, with an error below 2^-62 per term (far below FP64's rounding of a
+// 2^34-term sum).
 //
 // Sampling (inverse CDF): x_s = smallest i with C_i > u_s * T. The comparison
 // C_i * 2^53 > m_s * T, with u_s = m_s * 2^-53, is done exactly in 128-bit integers.
 //   1. k_block_sums: S_b = sum of q over block b (1024 amplitudes), one warp per block.
+//   2. k_scan_*:     exclusive prefix P_b of S_b, and T = sum_b S_b.
+//   3. the sampler (below): the block of each shot by binary search of P, the shots
+//      grouped by block in stored order, then each block gathered and walked.
 //
 // Blocks, prefixes and the walk follow the caller's basis order also when the state is
 // stored in a permuted qubit layout (caller bit q at stored bit to[q]): then block b is
@@ -20,13 +24,8 @@
 // bits P = {to[0..9]}. k_block_sums_map reads tiles that vary in the stored bits
 // P u {0..5} (coalesced: lane = stored bits 1..5, a float4 = stored bit 0); each
 // lane's amplitudes then lie in one or two caller blocks, and lanes of the same block
-// are combined by shuffles. k_sample
-// gathers the chosen block in caller order. So x_s is the same index, for the same
-// uniform, whatever the layout.
-//   2. k_scan_*:     exclusive prefix P_b of S_b, and T = sum_b S_b.
-//   3. k_sample:     one warp per shot: Philox4x64-10 uniform, binary search of the
-//                    block with P_b + S_b crossing the target, warp prefix over the
-//                    block's 32-amplitude lane ranges, sequential walk in one lane.
+// are combined by shuffles. The sampler gathers the chosen block in caller order. So
+// x_s is the same index, for the same uniform, whatever the layout.
 // XEB: k_xeb_partial / k_xeb_final gather |psi_x|^2 in FP64 and reduce in a fixed
 // tree order, F = 2^n * mean / T - 1.
 #include <bit>
@@ -36,7 +35,7 @@
 
 namespace rcs {
 
-__device__ __forceinline__ uint64_t fx_amp(float2 a, int &bad) { return fx_sq(a.x, bad) + fx_sq(a.y, bad); }
+__device__ __forceinline__ uint64_t fx_amp(float2 a, uint32_t &seen) { return fx_sq(a.x, seen) + fx_sq(a.y, seen); }
 
 __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
 #pragma unroll
@@ -62,19 +61,19 @@ __global__ void __launch_bounds__(256) k_block_sums(const float2 *__restrict__ p
     const int lane = threadIdx.x & 31;
     const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
     const uint32_t nf4 = (1u << blog2) >> 1;  // float4 per block (blog2 >= 1)
-    int bad = 0;
+    uint32_t seen = 0;
     for (uint64_t b = uint64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); b < nblocks; b += warps) {
         const float4 *p4 = reinterpret_cast<const float4 *>(psi + (b << blog2));
         uint64_t s = 0;
 #pragma unroll 4
         for (uint32_t c = lane; c < nf4; c += 32) {
             float4 v = __ldg(p4 + c);
-            s += fx_sq(v.x, bad) + fx_sq(v.y, bad) + fx_sq(v.z, bad) + fx_sq(v.w, bad);
+            s += fx_sq(v.x, seen) + fx_sq(v.y, seen) + fx_sq(v.z, seen) + fx_sq(v.w, seen);
         }
         s = warp_sum_u64(s);
         if (lane == 0) bsum[b] = s;
     }
-    if (bad) atomicOr(d_err, 1);
+    if (fx_overflow(seen)) atomicOr(d_err, 1);
 }
 
 // Layout form: tile t = all amplitudes whose stored bits outside `tsmask` = P u {0..5}
@@ -89,7 +88,7 @@ __global__ void __launch_bounds__(256) k_block_sums_map(const float2 *__restrict
                                                          uint64_t *__restrict__ bsum, int *__restrict__ d_err) {
     const int lane = threadIdx.x & 31;
     const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
-    int bad = 0;
+    uint32_t seen = 0;
     for (uint64_t t = uint64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); t < ntiles; t += warps) {
         uint64_t base = 0;
         for (int bit = 0, k = 0; bit < n; ++bit)
@@ -108,8 +107,8 @@ __global__ void __launch_bounds__(256) k_block_sums_map(const float2 *__restrict
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                s0 += fx_sq(v[u].x, bad) + fx_sq(v[u].y, bad);
-                s1 += fx_sq(v[u].z, bad) + fx_sq(v[u].w, bad);
+                s0 += fx_sq(v[u].x, seen) + fx_sq(v[u].y, seen);
+                s1 += fx_sq(v[u].z, seen) + fx_sq(v[u].w, seen);
             }
         } while (off != 0);
         if (b0p) s0 += s1;
@@ -124,7 +123,7 @@ __global__ void __launch_bounds__(256) k_block_sums_map(const float2 *__restrict
             if (!b0p) bsum[map_bits(to_caller, base | 1ull) >> blog2] = s1;
         }
     }
-    if (bad) atomicOr(d_err, 1);
+    if (fx_overflow(seen)) atomicOr(d_err, 1);
 }
 
 int launch_block_sums(const void *psi, int n, uint64_t *bsum, int *d_err, const BitMap &to_stored, void *stream) {
@@ -217,9 +216,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_top(uint64_t *__restrict_
     if (overflow) atomicOr(d_err, 2);
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint64_t *__restrict__ x, uint64_t count,
+// x and out may be the same array (each thread reads its entries before writing them).
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint64_t *x, uint64_t count,
                                                               const uint64_t *__restrict__ chunk_off,
-                                                              uint64_t *__restrict__ out) {
+                                                              uint64_t *out) {
     const uint64_t base = uint64_t(blockIdx.x) * kScanChunk + uint64_t(threadIdx.x) * kScanPer;
     uint64_t v[kScanPer], s = 0;
 #pragma unroll
@@ -283,19 +283,104 @@ __device__ __forceinline__ bool above(uint64_t a, uint64_t rhi, uint64_t rlo) {
 }
 
 // ---------------------------------------------------------------- sampler
+//
+// A call runs four kernels and the scan:
+//   k_sample_locate  one thread per shot: the target u_s T, the binary search of the block
+//                    prefix for the block b that holds it (out[s] = b), and a count of the
+//                    shot under key(b) in hist.
+//   scan             hist -> the first position of each key's shots (in place).
+//   k_sample_order   one thread per shot: order[position] = s, shots grouped by key.
+//   k_sample_resolve one warp per position: the shot's block is gathered in caller order and
+//                    walked (warp prefix over the 32 lanes' ranges, then one lane), and the
+//                    index replaces out[s].
+// key(b) is b's rank in the stored order of blocks: the block-index bits read from the
+// stored positions of caller bits 10.., low stored bits first (identity layout: key = b).
+// Blocks whose amplitudes share cache lines (they differ only in stored bits 0..3) then
+// have adjacent keys, and their shots are resolved by neighbouring warps while the lines
+// are in L2. In a permuted layout a block's 1024 amplitudes lie in up to 1024 lines, each
+// shared with up to 15 other blocks; resolved in shot order, every shot fetched all of its
+// lines from DRAM (about 115 KB per shot at 30 qubits).
+
+// smallest block b with inclusive prefix (bpre[b + 1], or T for the last) above the target
+__device__ __forceinline__ uint64_t find_block(const uint64_t *__restrict__ bpre, uint64_t nblocks, uint64_t rhi,
+                                               uint64_t rlo) {
+    uint64_t lo = 0, hi = nblocks - 1;
+    while (lo < hi) {
+        const uint64_t mid = lo + ((hi - lo) >> 1);  // mid + 1 <= hi < nblocks
+        if (above(bpre[mid + 1], rhi, rlo)) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+// u_s T as a 128-bit integer (rhi, rlo), u_s = m 2^-53
+__device__ __forceinline__ void shot_target(uint64_t g, uint64_t seed, uint64_t T, uint64_t &rhi, uint64_t &rlo) {
+    const uint64_t m = philox_word(g >> 2, seed, int(g & 3)) >> 11;
+    rlo = m * T;
+    rhi = __umul64hi(m, T);
+}
+
+__global__ void __launch_bounds__(256) k_sample_locate(const uint64_t *__restrict__ bpre, uint64_t nblocks,
+                                                        const uint64_t *__restrict__ total, uint64_t first,
+                                                        uint64_t shots, uint64_t seed, const BitMap key_map,
+                                                        uint64_t *__restrict__ out,
+                                                        unsigned long long *__restrict__ hist) {
+    const uint64_t T = *total;
+    const int lane = threadIdx.x & 31;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    // warp-uniform trip count: the per-key counts below are combined across the warp
+    for (uint64_t s0 = uint64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31u); s0 < shots; s0 += stride) {
+        const uint64_t s = s0 + uint64_t(lane);
+        uint64_t key = ~0ull;
+        if (s < shots) {
+            if (T == 0) {
+                out[s] = ~0ull;
+            } else {
+                uint64_t rhi, rlo;
+                shot_target(first + s, seed, T, rhi, rlo);
+                const uint64_t b = find_block(bpre, nblocks, rhi, rlo);
+                out[s] = b;
+                key = map_bits(key_map, b);
+            }
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        if (key != ~0ull && lane == __ffs(peers) - 1) atomicAdd(hist + key, (unsigned long long)__popc(peers));
+    }
+}
+
+// hist holds each key's first position; it is advanced as positions are taken
+__global__ void __launch_bounds__(256) k_sample_order(const uint64_t *__restrict__ total, uint64_t shots,
+                                                       const BitMap key_map, const uint64_t *__restrict__ out,
+                                                       unsigned long long *__restrict__ hist,
+                                                       uint64_t *__restrict__ order) {
+    if (*total == 0) return;
+    const int lane = threadIdx.x & 31;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t s0 = uint64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31u); s0 < shots; s0 += stride) {
+        const uint64_t s = s0 + uint64_t(lane);
+        const uint64_t key = s < shots ? map_bits(key_map, out[s]) : ~0ull;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        const int leader = __ffs(peers) - 1;
+        unsigned long long base = 0;
+        if (key != ~0ull && lane == leader) base = atomicAdd(hist + key, (unsigned long long)__popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (key != ~0ull) order[base + __popc(peers & ((1u << lane) - 1u))] = s;
+    }
+}
 
 // smap: caller index -> stored index (identity: the plain contiguous block reads).
-__global__ void __launch_bounds__(256) k_sample(const float2 *__restrict__ psi, int blog2, uint64_t nblocks,
-                                                 const uint64_t *__restrict__ bsum,
-                                                 const uint64_t *__restrict__ bpre,
-                                                 const uint64_t *__restrict__ total, uint64_t first, uint64_t shots,
-                                                 uint64_t seed,
-                                                 uint64_t *__restrict__ out, const BitMap smap) {
+__global__ void __launch_bounds__(256) k_sample_resolve(const float2 *__restrict__ psi, int blog2,
+                                                         const uint64_t *__restrict__ bpre,
+                                                         const uint64_t *__restrict__ total, uint64_t first,
+                                                         uint64_t shots, uint64_t seed,
+                                                         const uint64_t *__restrict__ order, uint64_t *out,
+                                                         const BitMap smap) {
+    const uint64_t T = *total;
+    if (T == 0) return;  // every out[s] is already ~0
     const int lane = threadIdx.x & 31;
     const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
-    const uint64_t T = *total;
     const uint32_t bamps = 1u << blog2;
-    int bad = 0;
+    uint32_t seen = 0;
     // layout: stored offset of caller offset 32 lane + a = lmap | emap[a] (disjoint bits)
     __shared__ uint64_t emap[32];
     uint64_t lmap = 0;
@@ -310,38 +395,27 @@ __global__ void __launch_bounds__(256) k_sample(const float2 *__restrict__ psi, 
             if (((32u * uint32_t(lane)) >> q) & 1u) lmap |= 1ull << smap.to[q];
         __syncthreads();
     }
-    for (uint64_t s = uint64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); s < shots; s += warps) {
-        if (T == 0) {
-            if (lane == 0) out[s] = ~0ull;
-            continue;
-        }
-        const uint64_t g = first + s;  // index of the shot in the stream of this seed
-        const uint64_t m = philox_word(g >> 2, seed, int(g & 3)) >> 11;  // u = m * 2^-53
-        const uint64_t rlo = m * T, rhi = __umul64hi(m, T);
-        // smallest block whose inclusive prefix crosses the target
-        uint64_t lo = 0, hi = nblocks - 1;
-        while (lo < hi) {
-            const uint64_t mid = lo + ((hi - lo) >> 1);
-            if (above(bpre[mid] + bsum[mid], rhi, rlo)) hi = mid;
-            else lo = mid + 1;
-        }
-        const uint64_t b = lo;
+    for (uint64_t i = uint64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); i < shots; i += warps) {
+        const uint64_t s = order[i];
+        const uint64_t b = out[s];  // read by every lane before lane 0 overwrites it below
+        uint64_t rhi, rlo;
+        shot_target(first + s, seed, T, rhi, rlo);
         const uint64_t base = bpre[b];
         const uint32_t a0 = uint32_t(lane) * 32u;
+        uint64_t idx = 0;
         if (!smap.identity) {  // blog2 = 10: every lane owns 32 caller offsets
             const float2 *lb = psi + (map_bits(smap, b << blog2) | lmap);
             uint64_t ls = 0;
 #pragma unroll 8
-            for (int a = 0; a < 32; ++a) ls += fx_amp(__ldg(lb + emap[a]), bad);
+            for (int a = 0; a < 32; ++a) ls += fx_amp(__ldg(lb + emap[a]), seen);
             const uint64_t incl = warp_incl_scan_u64(ls, lane);
             const unsigned hit = __ballot_sync(0xffffffffu, above(base + incl, rhi, rlo));
-            const int L = __ffs(hit) - 1;
-            uint64_t idx = 0;
+            const int L = __ffs(hit) - 1;  // hit != 0: lane 31's prefix is the block's inclusive prefix
             if (lane == L) {
                 uint64_t run = base + incl - ls;
                 idx = (b << blog2) + a0 + 31;
                 for (int a = 0; a < 32; ++a) {
-                    run += fx_amp(lb[emap[a]], bad);
+                    run += fx_amp(lb[emap[a]], seen);
                     if (above(run, rhi, rlo)) {
                         idx = (b << blog2) + a0 + uint32_t(a);
                         break;
@@ -349,35 +423,30 @@ __global__ void __launch_bounds__(256) k_sample(const float2 *__restrict__ psi, 
                 }
             }
             idx = __shfl_sync(0xffffffffu, idx, L < 0 ? 0 : L);
-            if (lane == 0) out[s] = idx;
-            continue;
-        }
-        const float2 *blk = psi + (b << blog2);
-        uint64_t ls = 0;
-        if (a0 < bamps) {
-            const uint32_t cnt = bamps - a0 < 32u ? bamps - a0 : 32u;
+        } else {
+            const float2 *blk = psi + (b << blog2);
+            uint64_t ls = 0;
+            const uint32_t cnt = a0 < bamps ? (bamps - a0 < 32u ? bamps - a0 : 32u) : 0u;
             for (uint32_t a = 0; a < cnt; a += 2) {
                 const float4 v = __ldg(reinterpret_cast<const float4 *>(blk + a0 + a));
-                ls += fx_sq(v.x, bad) + fx_sq(v.y, bad) + fx_sq(v.z, bad) + fx_sq(v.w, bad);
+                ls += fx_sq(v.x, seen) + fx_sq(v.y, seen) + fx_sq(v.z, seen) + fx_sq(v.w, seen);
             }
-        }
-        const uint64_t incl = warp_incl_scan_u64(ls, lane);
-        const unsigned hit = __ballot_sync(0xffffffffu, above(base + incl, rhi, rlo));
-        const int L = __ffs(hit) - 1;  // hit != 0: lane 31's prefix is P_b + S_b
-        uint64_t idx = 0;
-        if (lane == L) {
-            uint64_t run = base + incl - ls;
-            const uint32_t cnt = bamps - a0 < 32u ? bamps - a0 : 32u;
-            idx = (b << blog2) + a0 + cnt - 1;
-            for (uint32_t a = 0; a < cnt; ++a) {
-                run += fx_amp(blk[a0 + a], bad);
-                if (above(run, rhi, rlo)) {
-                    idx = (b << blog2) + a0 + a;
-                    break;
+            const uint64_t incl = warp_incl_scan_u64(ls, lane);
+            const unsigned hit = __ballot_sync(0xffffffffu, above(base + incl, rhi, rlo));
+            const int L = __ffs(hit) - 1;
+            if (lane == L) {
+                uint64_t run = base + incl - ls;
+                idx = (b << blog2) + a0 + cnt - 1;
+                for (uint32_t a = 0; a < cnt; ++a) {
+                    run += fx_amp(blk[a0 + a], seen);
+                    if (above(run, rhi, rlo)) {
+                        idx = (b << blog2) + a0 + a;
+                        break;
+                    }
                 }
             }
+            idx = __shfl_sync(0xffffffffu, idx, L < 0 ? 0 : L);
         }
-        idx = __shfl_sync(0xffffffffu, idx, L < 0 ? 0 : L);
         if (lane == 0) out[s] = idx;
     }
 }
@@ -390,16 +459,45 @@ BitMap identity_map(int n) {
     return m;
 }
 
-int launch_sample(const void *psi, int n, const uint64_t *bsum, const uint64_t *bpre, const uint64_t *total,
-                  uint64_t first, uint64_t shots, uint64_t seed, uint64_t *d_out, const BitMap &to_stored,
-                  void *stream) {
+// Block b -> its rank among blocks in stored order: block bit j is caller bit bl + j,
+// stored at bit to[bl + j]; its key bit is the number of those stored bits below it.
+static BitMap block_key_map(int n, int bl, const BitMap &to_stored) {
+    BitMap k = identity_map(n - bl);
+    if (to_stored.identity) return k;
+    k.identity = 1;
+    for (int j = 0; j < n - bl; ++j) {
+        int rank = 0;
+        for (int i = 0; i < n - bl; ++i) rank += to_stored.to[bl + i] < to_stored.to[bl + j];
+        k.to[j] = uint8_t(rank);
+        if (rank != j) k.identity = 0;
+    }
+    return k;
+}
+
+int launch_sample(const void *psi, int n, uint64_t *hist, const uint64_t *bpre, const uint64_t *total,
+                  uint64_t *chunk, uint64_t first, uint64_t shots, uint64_t seed, uint64_t *d_out, uint64_t *order,
+                  int *d_err, const BitMap &to_stored, void *stream) {
     if (shots == 0) return RCS_OK;
     const int bl = block_log2(n);
     if (!to_stored.identity && bl < 10) return RCS_ERR_UNSUPPORTED;
+    auto st = static_cast<cudaStream_t>(stream);
     const uint64_t nblocks = 1ull << (n - bl);
-    const unsigned grid = grid_for(shots * 32, 256, device_sm_count(), 8);
-    k_sample<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<const float2 *>(psi), bl, nblocks, bsum,
-                                                                  bpre, total, first, shots, seed, d_out, to_stored);
+    const BitMap key_map = block_key_map(n, bl, to_stored);
+    const int sms = device_sm_count();
+    auto *h = reinterpret_cast<unsigned long long *>(hist);
+    cudaError_t e = cudaMemsetAsync(hist, 0, nblocks * sizeof(uint64_t), st);
+    if (e != cudaSuccess) return note_launch_error(__func__, e);
+    const unsigned g1 = grid_for(shots, 256, sms, 8);
+    k_sample_locate<<<g1, 256, 0, st>>>(bpre, nblocks, total, first, shots, seed, key_map, d_out, h);
+    // in place: the counts become each key's first position (the scan's total, the shot
+    // count, goes to the spare slot after the chunk totals)
+    const size_t nch = scan_chunks(n);
+    int rc = launch_block_scan(hist, hist, chunk, chunk + nch, n, d_err, stream);
+    if (rc != RCS_OK) return rc;
+    k_sample_order<<<g1, 256, 0, st>>>(total, shots, key_map, d_out, h, order);
+    const unsigned g2 = grid_for(shots * 32, 256, sms, 8);
+    k_sample_resolve<<<g2, 256, 0, st>>>(static_cast<const float2 *>(psi), bl, bpre, total, first, shots, seed, order,
+                                          d_out, to_stored);
     return launch_status(__func__);
 }
 

@@ -69,15 +69,16 @@ __device__ uint64_t cta_sum_u64_static(uint64_t v) {
 // Exact fixed-point |psi|^2 partial sums, one per CTA (grid-stride over float4 pairs).
 __global__ void __launch_bounds__(kThreads) k_static_norm(const float4 *__restrict__ psi4, uint64_t n4,
                                                            uint64_t *__restrict__ parts) {
-    int bad = 0;
+    uint32_t seen = 0;
     uint64_t s = 0;
     const uint64_t stride = uint64_t(gridDim.x) * kThreads;
     for (uint64_t i = uint64_t(blockIdx.x) * kThreads + threadIdx.x; i < n4; i += stride) {
         const float4 v = __ldg(psi4 + i);
-        s += rcs::fx_sq(v.x, bad) + rcs::fx_sq(v.y, bad) + rcs::fx_sq(v.z, bad) + rcs::fx_sq(v.w, bad);
+        s += rcs::fx_sq(v.x, seen) + rcs::fx_sq(v.y, seen) + rcs::fx_sq(v.z, seen) + rcs::fx_sq(v.w, seen);
     }
     const uint64_t r = cta_sum_u64_static(s);
-    if (threadIdx.x == 0) parts[blockIdx.x] = bad ? ~0ull : r;
+    const int anybad = __syncthreads_or(rcs::fx_overflow(seen));
+    if (threadIdx.x == 0) parts[blockIdx.x] = anybad ? ~0ull : r;
 }
 
 // |psi_x|^2 summed in FP64 over 4096 samples per CTA; NaN marks an index >= 2^n.

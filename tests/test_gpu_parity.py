@@ -321,6 +321,56 @@ def test_planted_state_sampler_exact(lib, oracle):
         capi.rcs_destroy(ctx)
 
 
+def _floor_sq_2p62(x) -> int:
+    """floor(x^2 * 2^62) of a float32, exactly, from its integer significand and exponent."""
+    m, e = math.frexp(float(x))  # x = m 2^e, 0.5 <= |m| < 1 (exact for float32)
+    mi = int(abs(m) * 2**24)  # 24-bit integer significand: x = mi 2^(e - 24)
+    sh = 2 * (e - 24) + 62
+    return (mi * mi) << sh if sh >= 0 else (mi * mi) >> -sh
+
+
+def test_fixed_point_norm_is_exact(lib):
+    """The norm is the exact sum of floor(x^2 2^62) over every float component: a state of
+    small amplitudes (every exponent from subnormal to 2^-16, random significands) whose sum
+    stays below 2^53 in those units reads back from rcs_norm without rounding; and single
+    amplitudes of 1, 0.75 and 1.5 give their exact squares."""
+    n = 16
+    rng = np.random.default_rng(5)
+    re = (rng.uniform(1, 2, 1 << n) * 2.0 ** rng.integers(-40, -22, 1 << n)).astype(np.float32)
+    im = (rng.uniform(1, 2, 1 << n) * 2.0 ** rng.integers(-40, -22, 1 << n)).astype(np.float32)
+    re[:8] = np.array([0.0, 1e-45, 2.0**-126, 2.0**-31, 2.0**-31 * 1.5, 2.0**-30, 2.0**-16, 2.0**-16 * 1.75],
+                      dtype=np.float32)
+    im[:4] = -re[4:8]
+    psi = re + 1j * im
+    want = sum(_floor_sq_2p62(v) for v in re) + sum(_floor_sq_2p62(v) for v in im)
+    assert want < 2**53
+    ctx = capi.rcs_create(n, capi.RCS_PREC_FP32_FUSED)
+    try:
+        capi.rcs_state_write(ctx, psi.astype(np.complex64))
+        assert capi.rcs_norm(ctx) * 2.0**62 == float(want)
+        for a in (1.0, 0.75, 1.5):
+            one = np.zeros(1 << n, dtype=np.complex64)
+            one[12345] = a
+            capi.rcs_state_write(ctx, one)
+            assert capi.rcs_norm(ctx) == a * a
+            assert np.all(capi.rcs_sample(ctx, 1000, seed=3) == 12345)
+    finally:
+        capi.rcs_destroy(ctx)
+
+
+def test_zero_state_sampler(lib):
+    """A state of norm 0 has no distribution to draw from: every shot reads 2^64 - 1."""
+    n = 14
+    ctx = capi.rcs_create(n, capi.RCS_PREC_FP32_FUSED)
+    try:
+        capi.rcs_state_write(ctx, np.zeros(1 << n, dtype=np.complex64))
+        assert capi.rcs_norm(ctx) == 0.0
+        xs = capi.rcs_sample(ctx, 5000, seed=1)
+        assert np.all(xs == np.uint64(2**64 - 1))
+    finally:
+        capi.rcs_destroy(ctx)
+
+
 @pytest.mark.parametrize("n", [1, 2, 3, 9, 10, 11])
 def test_small_and_ragged_states(lib, oracle, n):
     circ = C.generate(C.grid_for_n(n), cycles=3, seed=n)
