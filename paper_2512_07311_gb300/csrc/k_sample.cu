@@ -369,6 +369,14 @@ __global__ void __launch_bounds__(256) k_sample_order(const uint64_t *__restrict
 }
 
 // smap: caller index -> stored index (identity: the plain contiguous block reads).
+// Each CTA takes one contiguous range of positions and its warps step through it
+// together (warp w: positions start + w, start + w + 8, ...), so the blocks in flight on
+// an SM at any moment are neighbours in stored order and share their cache lines while
+// these are still in L1/L2; a grid-stride assignment let the warps drift apart by far
+// more than the lifetime of a line in L2.
+// Per shot: lane l sums its 32 caller offsets 32 l .. 32 l + 31 of the block, a warp
+// scan finds the lane L whose range crosses the target, then the 32 lanes load one
+// amplitude each of L's range and a second scan finds the index.
 __global__ void __launch_bounds__(256) k_sample_resolve(const float2 *__restrict__ psi, int blog2,
                                                          const uint64_t *__restrict__ bpre,
                                                          const uint64_t *__restrict__ total, uint64_t first,
@@ -378,7 +386,7 @@ __global__ void __launch_bounds__(256) k_sample_resolve(const float2 *__restrict
     const uint64_t T = *total;
     if (T == 0) return;  // every out[s] is already ~0
     const int lane = threadIdx.x & 31;
-    const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
+    const uint32_t nw = blockDim.x >> 5;
     const uint32_t bamps = 1u << blog2;
     uint32_t seen = 0;
     // layout: stored offset of caller offset 32 lane + a = lmap | emap[a] (disjoint bits)
@@ -395,59 +403,54 @@ __global__ void __launch_bounds__(256) k_sample_resolve(const float2 *__restrict
             if (((32u * uint32_t(lane)) >> q) & 1u) lmap |= 1ull << smap.to[q];
         __syncthreads();
     }
-    for (uint64_t i = uint64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); i < shots; i += warps) {
-        const uint64_t s = order[i];
-        const uint64_t b = out[s];  // read by every lane before lane 0 overwrites it below
-        uint64_t rhi, rlo;
-        shot_target(first + s, seed, T, rhi, rlo);
-        const uint64_t base = bpre[b];
-        const uint32_t a0 = uint32_t(lane) * 32u;
-        uint64_t idx = 0;
-        if (!smap.identity) {  // blog2 = 10: every lane owns 32 caller offsets
-            const float2 *lb = psi + (map_bits(smap, b << blog2) | lmap);
+    const uint64_t per = (shots + gridDim.x - 1) / gridDim.x;
+    const uint64_t beg = uint64_t(blockIdx.x) * per;
+    const uint64_t end = beg + per < shots ? beg + per : shots;
+    const int Lmax = int((bamps - 1u) >> 5);  // last lane that owns offsets (blocks hold <= 1024)
+    for (uint64_t r = beg; r < end; r += nw) {  // same trip count in every warp: the barrier below
+        const uint64_t i = r + (threadIdx.x >> 5);
+        if (i < end) {
+            const uint64_t s = order[i];
+            const uint64_t b = out[s];  // read by every lane before lane 0 overwrites it below
+            uint64_t rhi, rlo;
+            shot_target(first + s, seed, T, rhi, rlo);
+            const uint64_t base = bpre[b];
+            const uint32_t a0 = uint32_t(lane) * 32u;
             uint64_t ls = 0;
+            const float2 *lb;  // layout: the block's stored base; identity: the block itself
+            if (!smap.identity) {  // blog2 = 10: every lane owns 32 caller offsets
+                lb = psi + map_bits(smap, b << blog2);
+                const float2 *ll = lb + lmap;
 #pragma unroll 8
-            for (int a = 0; a < 32; ++a) ls += fx_amp(__ldg(lb + emap[a]), seen);
-            const uint64_t incl = warp_incl_scan_u64(ls, lane);
-            const unsigned hit = __ballot_sync(0xffffffffu, above(base + incl, rhi, rlo));
-            const int L = __ffs(hit) - 1;  // hit != 0: lane 31's prefix is the block's inclusive prefix
-            if (lane == L) {
-                uint64_t run = base + incl - ls;
-                idx = (b << blog2) + a0 + 31;
-                for (int a = 0; a < 32; ++a) {
-                    run += fx_amp(lb[emap[a]], seen);
-                    if (above(run, rhi, rlo)) {
-                        idx = (b << blog2) + a0 + uint32_t(a);
-                        break;
-                    }
+                for (int a = 0; a < 32; ++a) ls += fx_amp(__ldg(ll + emap[a]), seen);
+            } else {
+                lb = psi + (b << blog2);
+                const uint32_t cnt = a0 < bamps ? (bamps - a0 < 32u ? bamps - a0 : 32u) : 0u;
+                for (uint32_t a = 0; a < cnt; a += 2) {
+                    const float4 v = __ldg(reinterpret_cast<const float4 *>(lb + a0 + a));
+                    ls += fx_sq(v.x, seen) + fx_sq(v.y, seen) + fx_sq(v.z, seen) + fx_sq(v.w, seen);
                 }
             }
-            idx = __shfl_sync(0xffffffffu, idx, L < 0 ? 0 : L);
-        } else {
-            const float2 *blk = psi + (b << blog2);
-            uint64_t ls = 0;
-            const uint32_t cnt = a0 < bamps ? (bamps - a0 < 32u ? bamps - a0 : 32u) : 0u;
-            for (uint32_t a = 0; a < cnt; a += 2) {
-                const float4 v = __ldg(reinterpret_cast<const float4 *>(blk + a0 + a));
-                ls += fx_sq(v.x, seen) + fx_sq(v.y, seen) + fx_sq(v.z, seen) + fx_sq(v.w, seen);
-            }
-            const uint64_t incl = warp_incl_scan_u64(ls, lane);
+            uint64_t incl = warp_incl_scan_u64(ls, lane);
             const unsigned hit = __ballot_sync(0xffffffffu, above(base + incl, rhi, rlo));
-            const int L = __ffs(hit) - 1;
-            if (lane == L) {
-                uint64_t run = base + incl - ls;
-                idx = (b << blog2) + a0 + cnt - 1;
-                for (uint32_t a = 0; a < cnt; ++a) {
-                    run += fx_amp(blk[a0 + a], seen);
-                    if (above(run, rhi, rlo)) {
-                        idx = (b << blog2) + a0 + a;
-                        break;
-                    }
-                }
+            const int L = hit ? __ffs(hit) - 1 : Lmax;  // hit != 0: lane 31's prefix is the block's inclusive prefix
+            const uint64_t run0 = __shfl_sync(0xffffffffu, base + incl - ls, L);  // prefix before L's range
+            // lane j takes caller offset 32 L + j
+            const uint32_t aL = uint32_t(L) * 32u;
+            uint64_t v = 0;
+            if (!smap.identity) {
+                const uint64_t lmL = __shfl_sync(0xffffffffu, lmap, L);
+                v = fx_amp(__ldg(lb + (lmL | emap[lane])), seen);
+            } else if (aL + uint32_t(lane) < bamps) {
+                v = fx_amp(__ldg(lb + aL + uint32_t(lane)), seen);
             }
-            idx = __shfl_sync(0xffffffffu, idx, L < 0 ? 0 : L);
+            incl = warp_incl_scan_u64(v, lane);
+            const unsigned hit2 = __ballot_sync(0xffffffffu, above(run0 + incl, rhi, rlo));
+            const uint32_t cntL = bamps - aL < 32u ? bamps - aL : 32u;
+            const uint32_t j = hit2 ? uint32_t(__ffs(hit2) - 1) : cntL - 1;
+            if (lane == 0) out[s] = (b << blog2) + aL + j;
         }
-        if (lane == 0) out[s] = idx;
+        __syncthreads();  // keeps the CTA's warps on neighbouring positions
     }
 }
 
