@@ -487,6 +487,30 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
                 ++i;
             }
         }
+        // kSub: bit j of jnz = amplitude j of a slice can be nonzero (its target bits keep it in
+        // the sub-state). The others are 0 in every tile, so their stage entries and tensor-memory
+        // columns are written with zeros once here and never copied or converted again: a pass that
+        // admits x qubits copies and converts 2^-x of a normal pass's amplitudes.
+        uint64_t jnz = ~0ull;
+        if constexpr (kSub) {
+            jnz = 0;
+            for (int j = 0; j < D; ++j)
+                if (hi_off[j] != ~0ull) jnz |= 1ull << j;
+            float2 *stz = reinterpret_cast<float2 *>(sm + L::kStage0);
+            for (int b = 0; b < 2; ++b)
+                for (int jj = 0; jj < 32; ++jj) {
+                    const int j = 32 * h + jj;
+                    if (!((jnz >> j) & 1ull)) stz[b * (kStageBytes / 8) + j * M + srow] = make_float2(0.f, 0.f);
+                }
+            float2 zero16[16];
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) zero16[jj] = make_float2(0.f, 0.f);
+            for (int b = 0; b < 2; ++b)
+                for (int ch = 0; ch < 2; ++ch)
+                    if (((jnz >> (32 * h + 16 * ch)) & 0xffffull) == 0)
+                        put16(abase_of(b, h) + (uint32_t(32 * q) << 16), acol_in(h, ch), zero16);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        }
         auto issue = [&](uint32_t i, int b) {
             const uint64_t tile = uint64_t(blockIdx.x) + uint64_t(i) * gridDim.x;
             const uint64_t base = slice_base(tile * M + srow, t);
@@ -508,6 +532,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
 #pragma unroll 8
                 for (int jj = 0; jj < 32; ++jj) {
                     const int j = 32 * h + jj;
+                    if (!((jnz >> j) & 1ull)) continue;  // zero in every tile, already in the stage
                     const uint64_t cj_sub = hi_off[j];
                     const bool zero = zslice || cj_sub == ~0ull;
                     const float2 *src = zero ? a.sub : a.sub + (cb | cj_sub);
@@ -539,6 +564,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
             const uint32_t abase = abase_of(b, h) + (uint32_t(32 * q) << 16);
 #pragma unroll
             for (int ch = 0; ch < 2; ++ch) {  // 16 amplitudes (TMEM columns) at a time
+                if (((jnz >> (32 * h + 16 * ch)) & 0xffffull) == 0) continue;  // kSub: zero columns
                 float2 v[16];
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj) v[jj] = stage[(32 * h + 16 * ch + jj) * M + srow];
