@@ -129,10 +129,29 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// As mbar_try_wait, but a thread whose phase is not complete may be suspended until it
+// completes or kSuspendNs pass, instead of returning at once: a waiting warp then costs no
+// shared-memory traffic per poll, and the stores and copies of the working roles keep
+// the load/store unit (the kernel's busiest) to themselves.
+constexpr uint32_t kSuspendNs = 20000;
+__device__ __forceinline__ bool mbar_try_wait_suspend(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(kSuspendNs)
+        : "memory");
+    return ok != 0;
+}
 // Bounded wait: false if another role aborted or the wait ran out (which aborts).
+// kSuspend: park the waiting thread in the hardware (the BF16 variants measured about 1%
+// faster per pass with it; the TF32 variants, whose K-half hand-offs are shorter, slower).
+template <bool kSuspend>
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
     const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
+    while (!(kSuspend ? mbar_try_wait_suspend(bar, parity) : mbar_try_wait(bar, parity))) {
         if (*abort_flag) return false;
         if (clock64() - t0 > tc::kWaitCycles) {
             *abort_flag = 1;
@@ -146,9 +165,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
 // broadcast, then every lane performs its own (now immediately successful)
 // acquiring test so the whole warp is ordered after the phase. The phase cannot
 // move on before this warp arrives on its own barrier, so the test cannot miss it.
+template <bool kSuspend>
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
     int ok = 1;
-    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag) ? 1 : 0;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait<kSuspend>(bar, parity, abort_flag) ? 1 : 0;
     ok = __shfl_sync(0xffffffffu, ok, 0);
     if (ok) (void)mbar_try_wait(bar, parity);
     __syncwarp();
@@ -405,11 +425,11 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
         if constexpr (kTf32) {
             if (i < 1) return true;
             const uint32_t j = i - 1;
-            return warp_wait(h ? bar_done(int(j & 1)) : bar_done_a(int(j & 1)), (j >> 1) & 1, abort_flag);
+            return warp_wait<!kTf32>(h ? bar_done(int(j & 1)) : bar_done_a(int(j & 1)), (j >> 1) & 1, abort_flag);
         } else {
             if (i < 2) return true;
             const uint32_t j = i - 2;
-            return warp_wait(bar_done(int(j & 1)), (j >> 1) & 1, abort_flag);
+            return warp_wait<!kTf32>(bar_done(int(j & 1)), (j >> 1) & 1, abort_flag);
         }
     };
     // TMEM column of the A region for K half h (TF32) or the A_hi image (BF16).
@@ -598,7 +618,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
         if (my_tiles > 1) issue(1, 1);
         for (uint32_t i = 0; i < my_tiles; ++i) {
             const int b = i & 1;
-            if (!warp_wait(bar_loaded(b), (i >> 1) & 1, abort_flag)) break;
+            if (!warp_wait<!kTf32>(bar_loaded(b), (i >> 1) & 1, abort_flag)) break;
             if (!wait_a_free(i, h)) break;
             tc_fence_after();
             const float2 *stage = reinterpret_cast<const float2 *>(sm + L::kStage0 + b * kStageBytes);
@@ -619,7 +639,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
             // it (tiles 0 and 1 were issued up front); converting tile i first keeps its
             // MMA and epilogue running while tile i+1 is in flight
             if (i >= 1 && i + 1 < my_tiles) {
-                if (!warp_wait(bar_sfree(b ^ 1), ((i - 1) >> 1) & 1, abort_flag)) break;
+                if (!warp_wait<!kTf32>(bar_sfree(b ^ 1), ((i - 1) >> 1) & 1, abort_flag)) break;
                 issue(i + 1, b ^ 1);
             }
         }
@@ -642,7 +662,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
         };
         for (uint32_t i = 0; i < my_tiles; ++i) {
             const int b = i & 1;
-            if (!warp_wait(bar_done(b), (i >> 1) & 1, abort_flag)) break;
+            if (!warp_wait<!kTf32>(bar_done(b), (i >> 1) & 1, abort_flag)) break;
             tc_fence_after();
             const uint64_t tile = uint64_t(blockIdx.x) + uint64_t(i) * gridDim.x;
             const uint64_t base = slice_base(tile * M + srow, t);
@@ -683,7 +703,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
         const uint32_t csr = cs[srow];
         for (uint32_t i = 0; i < my_tiles; ++i) {
             const int b = i & 1;
-            if (!warp_wait(bar_done(b), (i >> 1) & 1, abort_flag)) break;
+            if (!warp_wait<!kTf32>(bar_done(b), (i >> 1) & 1, abort_flag)) break;
             tc_fence_after();
             float2 *stage = reinterpret_cast<float2 *>(sm + L::kStage0 + b * kStageBytes);
             const uint32_t dbase = dcol_of(b) + (uint32_t(32 * q) << 16);
@@ -700,7 +720,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
                 mbar_arrive(bar_free(b));
                 mbar_arrive(bar_outready(b));
             }
-            if (!warp_wait(bar_outready(b), (i >> 1) & 1, abort_flag)) break;
+            if (!warp_wait<!kTf32>(bar_outready(b), (i >> 1) & 1, abort_flag)) break;
             const uint64_t tile = uint64_t(blockIdx.x) + uint64_t(i) * gridDim.x;
             const uint64_t tbase = slice_base(tile * M, t);
 #pragma unroll 8
@@ -726,8 +746,8 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
             for (uint32_t i = 0; i < my_tiles; ++i) {
                 const int b = i & 1;
                 const uint32_t par = (i >> 1) & 1;
-                if (!mbar_wait(bar_full(b), par, abort_flag)) break;
-                if (i >= 2 && !mbar_wait(bar_free(b), ((i >> 1) - 1) & 1, abort_flag)) break;
+                if (!mbar_wait<!kTf32>(bar_full(b), par, abort_flag)) break;
+                if (i >= 2 && !mbar_wait<!kTf32>(bar_free(b), ((i >> 1) - 1) & 1, abort_flag)) break;
                 tc_fence_after();
                 const uint32_t dcol = dcol_of(b), acol = acol_of(b);
                 if constexpr (kTf32) {
@@ -755,7 +775,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
                     };
                     half(0);
                     commit(bar_done_a(b), par);
-                    if (!mbar_wait(bar_full1(b), par, abort_flag)) break;
+                    if (!mbar_wait<!kTf32>(bar_full1(b), par, abort_flag)) break;
                     tc_fence_after();
                     half(1);
                 } else {
