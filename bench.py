@@ -29,11 +29,10 @@ sys.path.insert(0, ROOT)
 from paper_2512_07311_gb300 import circuits as C  # noqa: E402
 
 METRIC = "34q 20-cycle circuit time (s), shots/s; fused-TC vs plain FP32 at 1e-5 infid"
-# DRAM bytes (read + write) per amplitude per tensor-core pass, from ncu captures of full passes
-# on a 2^27-amplitude state (BF16x3: mean of seven passes, 2.089 GB per launch; TF32x3: two passes,
-# 2.0915 GB); the traffic of a pass is proportional to the state size, so a launch at n qubits moves
-# this x 2^n.
-TC_DRAM_BYTES_PER_AMP = {"bf16x3": 2.089e9 / 2**27, "tf32x3": 2.0915e9 / 2**27}
+# DRAM bytes (read + write) per amplitude per tensor-core pass, from ncu captures of the first seven
+# full passes on a 2^27-amplitude state (mean per launch: BF16x3 2.0854 GB, TF32x3 2.0852 GB); the
+# traffic of a pass is proportional to the state size, so a launch at n qubits moves this x 2^n.
+TC_DRAM_BYTES_PER_AMP = {"bf16x3": 2.0854e9 / 2**27, "tf32x3": 2.0852e9 / 2**27}
 WORKLOAD = "34q_5x7m1_20cyc"
 
 
