@@ -113,8 +113,9 @@ typedef struct {
     double flops;         /* algorithmic real flops of all passes (x3 for the split-precision path) */
     int64_t prefix_passes; /* leading passes a run from |0...0> does on compact sub-states (0: none) */
     int32_t prefix_qubits; /* qubits of the widest (last) sub-state */
-    int32_t prefix_stages; /* sub-states, nested and growing, each expanded into the next; the last
-                              expands into the full state */
+    int32_t prefix_stages; /* sub-states, nested and growing, each expanded into the next; the first
+                              full pass reads the last one directly where its kernel allows, else it
+                              is expanded into the full state */
 } rcs_plan_stats;
 
 /* ------------------------------------------------------------------ context */
@@ -122,7 +123,7 @@ typedef struct {
 /* Creates a context for n = rows*cols - n_removed qubits (1 <= n <= 34) on the
  * current CUDA device and sets the state to |0...0> (Section 3.2 item 1 starts
  * from the all-zero state of the circuit's qubits). Allocates 8 * 2^n bytes of
- * state plus the sampler's block sums (2^n / 1024 * 24 bytes). opts may be NULL
+ * state plus the sampler's block sums and prefix (2^n / 1024 * 16 bytes). opts may be NULL
  * (FP32_FUSED, k_max 4, legacy stream). Returns RCS_ERR_OOM if the state does
  * not fit in device memory. */
 int rcs_create(const rcs_grid *grid, const rcs_opts *opts, rcs_ctx **out);
@@ -139,11 +140,12 @@ int rcs_num_qubits(const rcs_ctx *ctx);
 /* Changes the stream used for the context's device work (cudaStream_t). */
 int rcs_set_stream(rcs_ctx *ctx, uint64_t stream);
 
-/* Resets the state to |0...0>. Lazy: no kernel runs now. A fused circuit started
- * from |0...0> runs its leading passes -- those whose targets span at most n - 4
- * qubits, since every other qubit is still |0> -- on a compact sub-state and writes
- * the whole state in one expansion pass; any other first use fills the state with
- * |0...0> first. */
+/* Resets the state to |0...0>. Lazy: no kernel runs now. A tensor-core or fused
+ * circuit started from |0...0> runs its leading passes on compact sub-states (the
+ * qubits they have not touched yet are still |0>): the planner picks up to two
+ * nested stages, each expanded into the next, and the first full pass reads the
+ * last sub-state itself, writing the whole state. Any other first use fills the
+ * state with |0...0> first. */
 int rcs_reset(rcs_ctx *ctx);
 
 /* ------------------------------------------------------------------ state construction (Section 3.2 item 1) */
