@@ -289,10 +289,10 @@ __device__ __forceinline__ bool above(uint64_t a, uint64_t rhi, uint64_t rlo) {
 //                    prefix for the block b that holds it (out[s] = b), and a count of the
 //                    shot under key(b) in hist.
 //   scan             hist -> the first position of each key's shots (in place).
-//   k_sample_order   one thread per shot: order[position] = s, shots grouped by key.
+//   k_sample_order   one thread per shot: order[position] = (b, s), shots grouped by key.
 //   k_sample_resolve one warp per position: the shot's block is gathered in caller order and
-//                    walked (warp prefix over the 32 lanes' ranges, then one lane), and the
-//                    index replaces out[s].
+//                    walked (warp prefix over the 32 lanes' ranges, then over the crossing
+//                    lane's 32 amplitudes), and the index replaces out[s].
 // key(b) is b's rank in the stored order of blocks: the block-index bits read from the
 // stored positions of caller bits 10.., low stored bits first (identity layout: key = b).
 // Blocks whose amplitudes share cache lines (they differ only in stored bits 0..3) then
@@ -348,7 +348,8 @@ __global__ void __launch_bounds__(256) k_sample_locate(const uint64_t *__restric
     }
 }
 
-// hist holds each key's first position; it is advanced as positions are taken
+// hist holds each key's first position; it is advanced as positions are taken.
+// order[position] = (b << 32) | s: the shot and its block (s < 2^31 per launch, b < 2^24).
 __global__ void __launch_bounds__(256) k_sample_order(const uint64_t *__restrict__ total, uint64_t shots,
                                                        const BitMap key_map, const uint64_t *__restrict__ out,
                                                        unsigned long long *__restrict__ hist,
@@ -358,13 +359,14 @@ __global__ void __launch_bounds__(256) k_sample_order(const uint64_t *__restrict
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     for (uint64_t s0 = uint64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31u); s0 < shots; s0 += stride) {
         const uint64_t s = s0 + uint64_t(lane);
-        const uint64_t key = s < shots ? map_bits(key_map, out[s]) : ~0ull;
+        const uint64_t b = s < shots ? out[s] : 0ull;
+        const uint64_t key = s < shots ? map_bits(key_map, b) : ~0ull;
         const unsigned peers = __match_any_sync(0xffffffffu, key);
         const int leader = __ffs(peers) - 1;
         unsigned long long base = 0;
         if (key != ~0ull && lane == leader) base = atomicAdd(hist + key, (unsigned long long)__popc(peers));
         base = __shfl_sync(0xffffffffu, base, leader);
-        if (key != ~0ull) order[base + __popc(peers & ((1u << lane) - 1u))] = s;
+        if (key != ~0ull) order[base + __popc(peers & ((1u << lane) - 1u))] = (b << 32) | s;
     }
 }
 
@@ -389,8 +391,10 @@ __global__ void __launch_bounds__(256) k_sample_resolve(const float2 *__restrict
     const uint32_t nw = blockDim.x >> 5;
     const uint32_t bamps = 1u << blog2;
     uint32_t seen = 0;
-    // layout: stored offset of caller offset 32 lane + a = lmap | emap[a] (disjoint bits)
+    // layout: stored offset of caller offset 32 lane + a = lmap | emap[a] (disjoint bits), and
+    // the stored base of block b = OR over its four 6-bit chunks c of btab[c][chunk value]
     __shared__ uint64_t emap[32];
+    __shared__ uint64_t btab[4][64];
     uint64_t lmap = 0;
     if (!smap.identity) {
         if (threadIdx.x < 32) {
@@ -398,6 +402,15 @@ __global__ void __launch_bounds__(256) k_sample_resolve(const float2 *__restrict
             for (int q = 0; q < 5; ++q)
                 if ((threadIdx.x >> q) & 1) e |= 1ull << smap.to[q];
             emap[threadIdx.x] = e;
+        }
+        {
+            const int c = int(threadIdx.x >> 6), v = int(threadIdx.x & 63u);  // 256 threads: one entry each
+            uint64_t e = 0;
+            for (int k = 0; k < 6; ++k) {
+                const int q = blog2 + 6 * c + k;
+                if (q < smap.n && ((v >> k) & 1)) e |= 1ull << smap.to[q];
+            }
+            btab[c][v] = e;
         }
         for (int q = 5; q < blog2; ++q)
             if (((32u * uint32_t(lane)) >> q) & 1u) lmap |= 1ull << smap.to[q];
@@ -410,8 +423,8 @@ __global__ void __launch_bounds__(256) k_sample_resolve(const float2 *__restrict
     for (uint64_t r = beg; r < end; r += nw) {  // same trip count in every warp: the barrier below
         const uint64_t i = r + (threadIdx.x >> 5);
         if (i < end) {
-            const uint64_t s = order[i];
-            const uint64_t b = out[s];  // read by every lane before lane 0 overwrites it below
+            const uint64_t sb = order[i];
+            const uint64_t s = sb & 0xffffffffull, b = sb >> 32;
             uint64_t rhi, rlo;
             shot_target(first + s, seed, T, rhi, rlo);
             const uint64_t base = bpre[b];
@@ -419,9 +432,10 @@ __global__ void __launch_bounds__(256) k_sample_resolve(const float2 *__restrict
             uint64_t ls = 0;
             const float2 *lb;  // layout: the block's stored base; identity: the block itself
             if (!smap.identity) {  // blog2 = 10: every lane owns 32 caller offsets
-                lb = psi + map_bits(smap, b << blog2);
+                lb = psi + (btab[0][b & 63u] | btab[1][(b >> 6) & 63u] | btab[2][(b >> 12) & 63u] |
+                            btab[3][(b >> 18) & 63u]);
                 const float2 *ll = lb + lmap;
-#pragma unroll 8
+#pragma unroll 16
                 for (int a = 0; a < 32; ++a) ls += fx_amp(__ldg(ll + emap[a]), seen);
             } else {
                 lb = psi + (b << blog2);
@@ -488,19 +502,26 @@ int launch_sample(const void *psi, int n, uint64_t *hist, const uint64_t *bpre, 
     const BitMap key_map = block_key_map(n, bl, to_stored);
     const int sms = device_sm_count();
     auto *h = reinterpret_cast<unsigned long long *>(hist);
-    cudaError_t e = cudaMemsetAsync(hist, 0, nblocks * sizeof(uint64_t), st);
-    if (e != cudaSuccess) return note_launch_error(__func__, e);
-    const unsigned g1 = grid_for(shots, 256, sms, 8);
-    k_sample_locate<<<g1, 256, 0, st>>>(bpre, nblocks, total, first, shots, seed, key_map, d_out, h);
-    // in place: the counts become each key's first position (the scan's total, the shot
-    // count, goes to the spare slot after the chunk totals)
     const size_t nch = scan_chunks(n);
-    int rc = launch_block_scan(hist, hist, chunk, chunk + nch, n, d_err, stream);
-    if (rc != RCS_OK) return rc;
-    k_sample_order<<<g1, 256, 0, st>>>(total, shots, key_map, d_out, h, order);
-    const unsigned g2 = grid_for(shots * 32, 256, sms, 8);
-    k_sample_resolve<<<g2, 256, 0, st>>>(static_cast<const float2 *>(psi), bl, bpre, total, first, shots, seed, order,
-                                          d_out, to_stored);
+    // at most 2^31 shots per round, so that a position's record packs the shot and its block
+    // (the block index has at most 24 bits for n <= 34)
+    constexpr uint64_t kRound = 1ull << 31;
+    for (uint64_t off = 0; off < shots; off += kRound) {
+        const uint64_t cnt = shots - off < kRound ? shots - off : kRound;
+        uint64_t *out = d_out + off;
+        cudaError_t e = cudaMemsetAsync(hist, 0, nblocks * sizeof(uint64_t), st);
+        if (e != cudaSuccess) return note_launch_error(__func__, e);
+        const unsigned g1 = grid_for(cnt, 256, sms, 8);
+        k_sample_locate<<<g1, 256, 0, st>>>(bpre, nblocks, total, first + off, cnt, seed, key_map, out, h);
+        // in place: the counts become each key's first position (the scan's total, the shot
+        // count, goes to the spare slot after the chunk totals)
+        int rc = launch_block_scan(hist, hist, chunk, chunk + nch, n, d_err, stream);
+        if (rc != RCS_OK) return rc;
+        k_sample_order<<<g1, 256, 0, st>>>(total, cnt, key_map, out, h, order);
+        const unsigned g2 = grid_for(cnt * 32, 256, sms, 8);
+        k_sample_resolve<<<g2, 256, 0, st>>>(static_cast<const float2 *>(psi), bl, bpre, total, first + off, cnt, seed,
+                                              order, out, to_stored);
+    }
     return launch_status(__func__);
 }
 
