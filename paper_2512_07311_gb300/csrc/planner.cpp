@@ -515,11 +515,15 @@ Blocking plan_blocks(int n, const std::vector<HostGate> &gates, int k_max, bool 
     const size_t nport = G ? std::size(variants) : 1;
     std::vector<std::vector<Block>> port(nport);
     std::vector<Cand> cands(configs.size());
-    parallel_for(nport + cands.size(), [&](size_t task) {
-        if (task < nport) {
+    // the staged candidates (each about 10 ms of beam search) are handed out first, the short
+    // greedy portfolio runs (a few ms each) fill in behind them
+    parallel_for(nport + cands.size(), [&](size_t t) {
+        if (t >= cands.size()) {
+            const size_t task = t - cands.size();
             port[task] = blocking(d, G, k_max, variants[task].first, variants[task].second);
             return;
         }
+        const size_t task = t + nport;
         const std::vector<int> &ks = configs[task - nport];
         Cand c;
         c.ks = ks;
