@@ -355,6 +355,18 @@ const char *rcs_batch_last_error(const rcs_batch *batch);
 /* Frees the batch (synchronises the device first). NULL is a no-op. */
 void rcs_batch_destroy(rcs_batch *batch);
 
+/* The whole batch in one synchronous call: circuit i has grids[i] (its qubit count
+ * rows*cols - n_removed, 2..30), the host gate list gates[i][0 .. n_gates[i]-1],
+ * shots[i] shots and sampling seed seeds[i]. Creates a batch with opts (engine as in
+ * rcs_batch_create; NULL = the persistent FP32 engine), runs it once on opts->stream,
+ * copies circuit i's samples to out_bits[i] (shots[i] uint64, HOST) and its XEB to
+ * out_xeb[i] (HOST), and frees everything. out_bits, any out_bits[i], or out_xeb may
+ * be NULL to skip that output. Errors as the calls it is made of; the message is in
+ * rcs_last_error(NULL). */
+int rcs_batch_run(const rcs_grid *grids, const rcs_gate *const *gates, const size_t *n_gates, size_t n_inst,
+                  const uint64_t *shots, const uint64_t *seeds, uint64_t **out_bits, double *out_xeb,
+                  const rcs_opts *opts);
+
 /* ------------------------------------------------------------------ allocation-free scoring */
 
 /* Linear XEB, as rcs_xeb_device, for callers that cannot allocate device memory:

@@ -101,6 +101,9 @@ SIGNATURES = [
     ("rcs_batch_set_fault", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double]),
     ("rcs_batch_last_error", ctypes.c_char_p, [_P]),
     ("rcs_batch_destroy", None, [_P]),
+    ("rcs_batch_run", ctypes.c_int, [ctypes.POINTER(rcs_grid), ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_size_t),
+                                     ctypes.c_size_t, _u64p, _u64p, ctypes.POINTER(_u64p), _f64p,
+                                     ctypes.POINTER(rcs_opts)]),
     ("rcs_xeb_static", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
                                       ctypes.c_void_p, ctypes.c_uint64]),
 ]
@@ -396,3 +399,32 @@ def rcs_batch_set_fault(batch, skip_item: int, wait_limit_s: float = 2.0):
 
 def rcs_batch_destroy(batch):
     load().rcs_batch_destroy(batch)
+
+
+def rcs_batch_run(items, precision: int = RCS_PREC_FP32_FUSED, k_max: int = 0, autotune: int = 1, stream: int = 0):
+    """items: iterable of (circuits.Grid, gates GATE_DTYPE array, shots, seed). One synchronous call
+    for the whole batch; returns [(samples uint64 array, xeb float)] per circuit."""
+    items = list(items)
+    m = len(items)
+    grids = (rcs_grid * m)()
+    gptrs = (_P * m)()
+    ngates = (ctypes.c_size_t * m)()
+    shots = np.array([it[2] for it in items], dtype=np.uint64)
+    seeds = np.array([it[3] for it in items], dtype=np.uint64)
+    outs = [np.zeros(int(s), dtype=np.uint64) for s in shots]
+    optr = (_u64p * m)(*[o.ctypes.data_as(_u64p) for o in outs])
+    xeb = np.zeros(m, dtype=np.float64)
+    keep = []
+    for i, (grid, gates, _, _) in enumerate(items):
+        rem = np.ascontiguousarray(grid.removed, dtype=np.int32)
+        keep.append(rem)
+        grids[i].rows, grids[i].cols, grids[i].n_removed = grid.rows, grid.cols, len(rem)
+        grids[i].removed = rem.ctypes.data_as(_i32p) if len(rem) else None
+        ptr, k = _gates_ptr(gates, None)
+        keep.append(k)
+        gptrs[i] = ptr
+        ngates[i] = len(k[0])
+    o = _opts(precision, k_max, stream, autotune)
+    _check(load().rcs_batch_run(grids, gptrs, ngates, m, shots.ctypes.data_as(_u64p), seeds.ctypes.data_as(_u64p),
+                                optr, xeb.ctypes.data_as(_f64p), ctypes.byref(o)))
+    return [(outs[i], float(xeb[i])) for i in range(m)]

@@ -101,6 +101,34 @@ def test_batch_wait_limit_reports_timeout(lib, oracle):
         capi.rcs_batch_destroy(b)
 
 
+@pytest.mark.parametrize("precision", [capi.RCS_PREC_FP32_FUSED, capi.RCS_PREC_BF16X3])
+def test_batch_run_one_call(lib, oracle, precision):
+    """rcs_batch_run (grids, gate lists, shots and seeds in, samples and XEB out, in one
+    call) gives the draws and scores of the same batch built and launched step by step,
+    and samples that follow each circuit's oracle distribution."""
+    circs = small_batch()[:4]
+    items = [(c.n_qubits, c.gates, 3000 + 1000 * i, 40 + i) for i, c in enumerate(circs)]
+    res = capi.rcs_batch_run([(c.grid, c.gates, sh, sd) for c, (_, _, sh, sd) in zip(circs, items)],
+                             precision=precision, k_max=4 if precision == capi.RCS_PREC_FP32_FUSED else 0,
+                             autotune=0)
+    b = capi.rcs_batch_create(items, k_max=4 if precision == capi.RCS_PREC_FP32_FUSED else 0, autotune=0,
+                              precision=precision)
+    try:
+        capi.rcs_batch_launch(b)
+        capi.rcs_batch_wait(b)
+        for i, (c, (_, _, sh, _)) in enumerate(zip(circs, items)):
+            xs, F = capi.rcs_batch_result(b, i, sh)
+            np.testing.assert_array_equal(res[i][0], xs)
+            assert res[i][1] == F
+            want = oracle.simulate(c.n_qubits, c.gates)
+            assert abs(F - oracle.xeb(want, xs)) <= 5e-3
+    finally:
+        capi.rcs_batch_destroy(b)
+    with pytest.raises(capi.RcsError) as e:
+        capi.rcs_batch_run([], precision=precision)
+    assert e.value.code == capi.RCS_ERR_ARG
+
+
 def test_batch_rejects_bad_input(lib):
     c = small_batch()[0]
     with pytest.raises(capi.RcsError):
