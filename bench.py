@@ -244,14 +244,8 @@ def run_batch(args, torch, capi):
             plan = capi.rcs_plan_build(n, c.gates, precision)
             pi = capi.rcs_plan_info(plan)
             capi.rcs_plan_destroy(plan)
-            pre, m = pi["prefix_passes"], pi["prefix_qubits"]
-            # sub-state passes (counted at the widest sub-state), then the first full pass reading
-            # the last sub-state (8 x 2^m in, 8 x 2^n out) and the other full passes; no prefix:
-            # reset (8 x 2^n) and full passes
-            if pre:
-                total += 16.0 * 2**m * pre + 8.0 * 2**m + 8.0 * 2**n + 16.0 * 2**n * (pi["n_passes"] - pre - 1)
-            else:
-                total += 8.0 * 2**n + 16.0 * 2**n * pi["n_passes"]
+            # each pass at the size of the state it runs on, the zero fill and the expansions
+            total += pi["zero_hbm_bytes"]
         return total
 
     prec = capi.PRECISIONS[args.precision]
@@ -442,8 +436,9 @@ def main():
             capi.rcs_sync(ctx)
             t = e0.elapsed_time(e1) / 1e3
             amps[name] = capi.rcs_amplitudes(ctx, subset)
+            # algorithmic bytes of the run from |0...0> (sub-state passes at their own size)
             compare[name] = {"apply_s": t, "passes": int(i2["n_passes"]),
-                             "hbm_frac": 16.0 * 2**n * i2["n_passes"] / t / 1e9 / peaks["hbm_gbs"]}
+                             "hbm_frac": i2["zero_hbm_bytes"] / t / 1e9 / peaks["hbm_gbs"]}
             capi.rcs_plan_destroy(p2)
 
         def subset_infidelity(a, b):

@@ -116,6 +116,8 @@ typedef struct {
     int32_t prefix_stages; /* sub-states, nested and growing, each expanded into the next; the first
                               full pass reads the last one directly where its kernel allows, else it
                               is expanded into the full state */
+    double zero_hbm_bytes; /* algorithmic HBM bytes of rcs_plan_run from |0...0>: each pass at the size
+                              of the state it runs on, the zero fill, the expansions */
 } rcs_plan_stats;
 
 /* ------------------------------------------------------------------ context */

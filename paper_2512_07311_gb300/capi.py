@@ -44,7 +44,8 @@ class rcs_plan_stats(ctypes.Structure):
     _fields_ = [("n_qubits", ctypes.c_int32), ("precision", ctypes.c_int32), ("n_gates", ctypes.c_int64),
                 ("n_passes", ctypes.c_int64), ("k_max", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("hbm_bytes", ctypes.c_double), ("flops", ctypes.c_double), ("prefix_passes", ctypes.c_int64),
-                ("prefix_qubits", ctypes.c_int32), ("prefix_stages", ctypes.c_int32)]
+                ("prefix_qubits", ctypes.c_int32), ("prefix_stages", ctypes.c_int32),
+                ("zero_hbm_bytes", ctypes.c_double)]
 
 
 class rcs_batch_item(ctypes.Structure):

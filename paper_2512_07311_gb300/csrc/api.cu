@@ -803,6 +803,25 @@ int rcs_plan_info(const rcs_plan *plan, rcs_plan_stats *out) {
     out->prefix_passes = plan_stages(p, &stages);
     out->prefix_qubits = stages.empty() ? 0 : std::popcount(stages.back().tmask);
     out->prefix_stages = int32_t(stages.size());
+    // what run_substages and the passes after it move, from |0...0>
+    if (stages.empty()) {
+        out->zero_hbm_bytes = 8.0 * amps + out->hbm_bytes;  // zero fill, then every pass on the full state
+    } else {
+        double z = 8.0 * std::ldexp(1.0, std::popcount(stages.front().tmask));  // first sub-state's zero fill
+        for (size_t si = 0; si < stages.size(); ++si) {
+            const double m = std::ldexp(1.0, std::popcount(stages[si].tmask));
+            z += 16.0 * m * double(stages[si].count);
+            if (si + 1 < stages.size()) z += 8.0 * m + 8.0 * std::ldexp(1.0, std::popcount(stages[si + 1].tmask));
+        }
+        // the last sub-state is read once into the full state: by the first full pass itself or by an
+        // expansion before it; either way 8 * 2^m in and 8 * 2^n out, plus 16 * 2^n per other full pass
+        const size_t after = size_t(out->prefix_passes);
+        const double mlast = std::ldexp(1.0, std::popcount(stages.back().tmask));
+        const bool fused = after < p.passes.size() && tc_pass_takes_substate(p.passes[after], p.n);
+        z += 8.0 * mlast + 8.0 * amps;
+        z += 16.0 * amps * double(p.passes.size() - after - (fused ? 1 : 0));
+        out->zero_hbm_bytes = z;
+    }
     return RCS_OK;
 }
 
