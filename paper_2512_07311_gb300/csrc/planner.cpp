@@ -221,14 +221,17 @@ struct Block {
 // taken first.
 Block grow(const Dag &d, std::vector<size_t> &head, int k_max, int window, int seed, uint64_t allow = ~0ull) {
     Block b;
-    std::vector<int> ready;
+    thread_local std::vector<int> ready;
     if (seed >= 0) {
         b.gates.push_back(seed);
         b.Q |= d.mask[seed];
         d.take(seed, head);
     }
+    // The ready set is kept up to date as gates are taken (taking a gate can only make the
+    // gates now at the heads of its own qubits ready); the choice below does not depend on
+    // the set's order (ties go to the lowest gate index).
+    d.ready_gates(head, &ready);
     for (;;) {
-        d.ready_gates(head, &ready);
         int best = -1, best_new = 1 << 30, best_aff = -1;
         for (int gi : ready) {
             if (d.mask[gi] & ~allow) continue;
@@ -257,6 +260,23 @@ Block grow(const Dag &d, std::vector<size_t> &head, int k_max, int window, int s
         b.gates.push_back(best);
         b.Q |= d.mask[best];
         d.take(best, head);
+        for (size_t i = 0; i < ready.size(); ++i)
+            if (ready[i] == best) {
+                ready[i] = ready.back();
+                ready.pop_back();
+                break;
+            }
+        const HostGate &x = (*d.g)[size_t(best)];
+        int added = -1;  // a gate at the head of both of best's qubits is added once
+        for (int a = 0; a < x.nq; ++a) {
+            const int q = x.q[a];
+            if (head[q] >= d.queue[q].size()) continue;
+            const int gi = d.queue[q][head[q]];
+            if (gi != added && d.ready(gi, head)) {
+                ready.push_back(gi);
+                added = gi;
+            }
+        }
     }
     return b;
 }
