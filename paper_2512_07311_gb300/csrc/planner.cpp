@@ -18,7 +18,7 @@
 #include <functional>
 #include <condition_variable>
 #include <atomic>
-#include <map>
+#include <unordered_set>
 #include <thread>
 
 #include "internal.h"
@@ -388,16 +388,21 @@ std::vector<Block> beam_blocking(const Dag &d, size_t G, int k_max, int window, 
             parallel_for(states.size(), work);
         }
         // merge equal frontiers (first occurrence in state order wins ties), keep the best `width`
-        std::map<std::vector<size_t>, std::pair<size_t, size_t>> seen;  // head -> (slot, index)
+        struct HeadHash {
+            size_t operator()(const std::vector<size_t> *h) const {
+                uint64_t x = 1469598103934665603ull;  // FNV-1a over the queue positions
+                for (size_t v : *h) x = (x ^ uint64_t(v)) * 1099511628211ull;
+                return size_t(x);
+            }
+        };
+        struct HeadEq {
+            bool operator()(const std::vector<size_t> *a, const std::vector<size_t> *b) const { return *a == *b; }
+        };
+        std::unordered_set<const std::vector<size_t> *, HeadHash, HeadEq> seen;
         std::vector<std::pair<size_t, size_t>> order;
         for (size_t i = 0; i < slot.size(); ++i)
-            for (size_t j = 0; j < slot[i].size(); ++j) {
-                auto it = seen.find(slot[i][j].head);
-                if (it == seen.end()) {
-                    seen.emplace(slot[i][j].head, std::make_pair(i, j));
-                    order.emplace_back(i, j);
-                }
-            }
+            for (size_t j = 0; j < slot[i].size(); ++j)
+                if (seen.insert(&slot[i][j].head).second) order.emplace_back(i, j);
         if (order.empty()) return {};
         std::stable_sort(order.begin(), order.end(), [&](const auto &x, const auto &y) {
             return slot[x.first][x.second].placed > slot[y.first][y.second].placed;
