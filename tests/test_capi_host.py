@@ -158,3 +158,42 @@ def test_zero_state_plan_uses_a_substate_prefix():
     for t, _ in passes[:pre]:
         union |= set(int(x) for x in t)
     assert len(union) <= m
+
+
+def test_zero_state_byte_count():
+    """rcs_plan_stats.zero_hbm_bytes, the algorithmic bytes of a run from |0...0>: with no
+    sub-state prefix it is exactly the zero fill plus 16 x 2^n per pass. With one, each stage's
+    passes count at that stage's size, plus the zero fill of the first sub-state, the expansions,
+    and the first full pass reading the last sub-state (8 x 2^m in, 8 x 2^n out): it lies between
+    the bounds that the passes' growing target union and the widest sub-state give."""
+    circ = C.config_circuit("34q_5x7m1_20cyc")
+    n = 34
+    plain = capi.rcs_plan_build(n, circ.gates, capi.RCS_PREC_FP32_PLAIN)
+    try:
+        info = capi.rcs_plan_info(plain)
+        assert info["prefix_passes"] == 0
+        assert info["zero_hbm_bytes"] == 8.0 * 2**n + 16.0 * 2**n * info["n_passes"]
+    finally:
+        capi.rcs_plan_destroy(plain)
+    plan = capi.rcs_plan_build(n, circ.gates, capi.RCS_PREC_BF16X3)
+    try:
+        info, passes = _plan_passes(plan)
+    finally:
+        capi.rcs_plan_destroy(plan)
+    pre = info["prefix_passes"]
+    assert pre > 0 and info["prefix_stages"] >= 1
+    # the union of targets after each prefix pass: no stage is narrower than the union of the
+    # targets so far (nor than 13 qubits, one tensor-core tile), none wider than the last
+    unions = []
+    u = set()
+    for t, _ in passes[:pre]:
+        u |= set(int(x) for x in t)
+        unions.append(len(u))
+    m_last = info["prefix_qubits"]
+    assert unions[-1] <= m_last
+    # every pass of the prefix runs on a state of at most m_last qubits and at least 13
+    lo = 8.0 * 2**13 + sum(16.0 * 2**max(13, s) for s in unions) + 8.0 * 2**m_last + 8.0 * 2**n
+    hi = 8.0 * 2**m_last + 16.0 * 2**m_last * pre + 8.0 * 2**m_last * 2 * info["prefix_stages"] + 8.0 * 2**n
+    full = 16.0 * 2**n * (info["n_passes"] - pre - 1)  # the first full pass reads the sub-state
+    assert lo + full <= info["zero_hbm_bytes"] <= hi + full
+    assert info["zero_hbm_bytes"] < info["hbm_bytes"]
