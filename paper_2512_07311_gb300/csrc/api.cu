@@ -330,8 +330,10 @@ void build_ops_images(Plan &plan, std::vector<uint8_t> *img) {
     for (size_t i = 0; i < plan.passes.size(); ++i)
         if (plan.passes[i].kind == PASS_TC) plan.tc_offset[i] = int64_t(per * count++);
     img->assign(per * count, 0);
-    for (size_t i = 0; i < plan.passes.size(); ++i)
+    // independent images in disjoint slices of the buffer
+    host_parallel_for(plan.passes.size(), [&](size_t i) {
         if (plan.tc_offset[i] >= 0) tc_build_ops(plan.passes[i], img->data() + plan.tc_offset[i], tf32);
+    });
 }
 
 int materialize(rcs_ctx *c) {

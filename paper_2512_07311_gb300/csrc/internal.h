@@ -3,6 +3,7 @@
 
 #include <complex>
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -21,6 +22,10 @@ int set_thread_error(int code, const std::string &msg);
 
 // Text of the last failed kernel launch on this thread (cleared by the call).
 std::string take_launch_error();
+
+// Runs f(0) .. f(count - 1) on the library's persistent host worker threads (the calling
+// thread takes part) and returns when all are done; f must be safe to run concurrently.
+void host_parallel_for(size_t count, const std::function<void(size_t)> &f);
 
 // ---- gates (gates.cpp)
 struct HostGate {

@@ -148,6 +148,8 @@ static void parallel_for(size_t count, F f) {
     TaskPool::get().run(count, std::function<void(size_t)>(f));
 }
 
+void host_parallel_for(size_t count, const std::function<void(size_t)> &f) { parallel_for(count, f); }
+
 static Pass make_pass(PassKind kind, uint64_t qmask, const std::vector<const HostGate *> &blk) {
     Pass p;
     p.kind = kind;
