@@ -52,6 +52,10 @@ def parse():
                     help="split precision of the tensor-core passes (bf16x3: the headline path)")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP32 plain/fused comparison runs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--oracle-check", action="store_true",
+                    help="also build the workload's whole state with the CPU oracle (timed: apply, sample, XEB) and "
+                         "compare every GPU path with it at full size; needs host memory for the complex128 state "
+                         "(30 q: 16 GiB, 32 q: 64 GiB) and its CDF")
     return ap.parse_args()
 
 
@@ -173,11 +177,84 @@ def cpu_baseline(circ: C.Circuit, shots: int, budget_s: float = 20.0) -> dict:
     scale = 2.0 ** (n - n_s)
     # sampling = one 2^n CDF pass (dominant) + shots * log2(2^n) searches; scale the pass by 2^(n-n_s)
     est = t_apply * scale * len(circ.gates) / max(done, 1) + t_sample * scale + t_xeb * shots / s_shots
-    return {"value": est, "unit": "s", "cores": O.threads(), "kind": "oracle",
+    return {"value": est, "unit": "s", "cores": O.threads(), "kind": "oracle", "measured": False,
             "sample": (f"oracle on a 2^{n_s}-amplitude complex128 state: first {done} of {len(circ.gates)} "
                        f"workload gates (qubit q -> q mod {n_s}), {s_shots} shots + XEB; "
                        f"scaled x2^{n - n_s} per amplitude pass and by gate count"),
             "measured_s": {"apply": t_apply, "sample": t_sample, "xeb": t_xeb}}
+
+
+def host_memory_bytes() -> int:
+    try:
+        return os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
+    except (ValueError, OSError):
+        return 0
+
+
+def oracle_check(circ: C.Circuit, shots: int, ctx, plans: dict, headline: str, capi) -> tuple[dict, dict]:
+    """The workload's whole complex128 oracle state, built and timed on the host cores,
+    against each GPU path in `plans` (name -> uploaded plan) run from |0...0> on ctx.
+    Returns (cpu_baseline measured on the full workload, comparison figures)."""
+    from oracle import fullsize as F
+    from oracle import oracle as O
+
+    O.build()
+    n = circ.n_qubits
+    need = 16 * 2**n * 2.5
+    if host_memory_bytes() < need:
+        return None, {"skipped": f"host memory {host_memory_bytes() / 2**30:.0f} GiB < {need / 2**30:.0f} GiB"}
+    seed = 31
+    t0 = time.perf_counter()
+    psi = O.simulate(n, circ.gates)
+    t_apply = time.perf_counter() - t0
+    rng = np.random.default_rng(2**20)
+    S = np.unique(rng.integers(0, 1 << n, size=1 << 20, dtype=np.uint64))
+    out = {"seed": seed, "shots": shots, "paths": {}}
+    xs = None
+    for name, plan in plans.items():
+        capi.rcs_reset(ctx)
+        capi.rcs_plan_run(ctx, plan)
+        capi.rcs_sync(ctx)
+        if name == headline:
+            xs = capi.rcs_sample(ctx, shots, seed)
+            F_gpu = capi.rcs_xeb(ctx, xs)
+        a = capi.rcs_amplitudes(ctx, S)
+        b = psi[S.astype(np.int64)]
+        sub = float(1.0 - abs(np.vdot(a, b)) ** 2 / (np.vdot(a, a).real * np.vdot(b, b).real))
+        cmp = F.compare_states(psi, lambda f, c: capi.rcs_state_read(ctx, f, c))
+        out["paths"][name] = {"infidelity": cmp["infidelity"], "subset_infidelity": sub,
+                              "max_abs_amp_err": cmp["max_abs_diff"],
+                              "norm": cmp["norm_other"]}
+    t1 = time.perf_counter()
+    x_or = O.sample(psi, shots, seed)
+    t_sample = time.perf_counter() - t1
+    t2 = time.perf_counter()
+    F_or_own = O.xeb(psi, x_or)
+    t_xeb = time.perf_counter() - t2
+    F_or = O.xeb(psi, xs)
+    eps = F.window_eps(out["paths"][headline]["infidelity"])
+    u = F.uniforms(seed, 0, shots)
+    out[headline] = {"xeb_gpu": F_gpu, "xeb_oracle_same_shots": F_or, "xeb_diff": abs(F_gpu - F_or),
+                     "xeb_oracle_own_shots": F_or_own,
+                     "draws_equal_oracle_own_state": float(np.mean(xs == x_or)),
+                     "draw_window_eps": eps,
+                     "draws_outside_oracle_window": F.draw_window_violations(psi, xs, u, eps)}
+    del psi, x_or
+    # the oracle's sampler on the headline path's own state (read back, promoted exactly)
+    capi.rcs_reset(ctx)
+    capi.rcs_plan_run(ctx, plans[headline])
+    capi.rcs_sync(ctx)
+    mine = np.empty(1 << n, dtype=np.complex128)
+    for f in range(0, 1 << n, F.CHUNK):
+        c = min(F.CHUNK, (1 << n) - f)
+        mine[f:f + c] = capi.rcs_state_read(ctx, f, c)
+    out[headline]["draws_equal_oracle_on_same_state"] = float(np.mean(O.sample(mine, shots, seed) == xs))
+    del mine
+    cpu = {"value": t_apply + t_sample + t_xeb, "unit": "s", "cores": O.threads(), "kind": "oracle",
+           "measured": True, "sample": f"the whole workload: {len(circ.gates)} gates on the 2^{n}-amplitude "
+                                       f"complex128 state, {shots} shots + XEB",
+           "measured_s": {"apply": t_apply, "sample": t_sample, "xeb": t_xeb}}
+    return cpu, out
 
 
 # ------------------------------------------------------------------ reference arm (the CPU oracle)
@@ -451,7 +528,19 @@ def main():
         compare["speedup_vs_fp32_plain"] = compare["fp32_plain"]["apply_s"] / compare[f"{args.precision}_apply_s"]
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
+    check = None
+    if args.oracle_check and rank == 0 and world == 1:
+        plans = {args.precision: plan}
+        extra = []
+        for name, p2prec in ((other, capi.PRECISIONS[other]), ("fp32_plain", capi.RCS_PREC_FP32_PLAIN)):
+            p2 = capi.rcs_plan_build(n, circ.gates, p2prec)
+            capi.rcs_plan_upload(ctx, p2)
+            plans[name] = p2
+            extra.append(p2)
+        cpu, check = oracle_check(circ, shots, ctx, plans, args.precision, capi)
+        for p2 in extra:
+            capi.rcs_plan_destroy(p2)
+    if cpu is None and rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(circ, shots)
 
     capi.rcs_plan_destroy(plan)
@@ -484,6 +573,8 @@ def main():
             "compare": compare,
             "cpu_baseline": cpu,
         }
+        if check is not None:
+            line["oracle_check"] = check
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

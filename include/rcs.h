@@ -213,7 +213,9 @@ void rcs_plan_destroy(rcs_plan *plan);
 /* ------------------------------------------------------------------ readout */
 
 /* Gathers amplitudes psi[bits[i]] into out_re_im[2i], out_re_im[2i+1] (complex64
- * promoted exactly to complex128). Synchronous. bits[i] < 2^n or RCS_ERR_ARG. */
+ * promoted exactly to complex128). Section 3.2 item 3: each sampling job logs the
+ * measurement amplitudes of its shots; this is that read-out of the built state
+ * for any list of bitstrings. Synchronous. bits[i] < 2^n or RCS_ERR_ARG. */
 int rcs_amplitudes(rcs_ctx *ctx, const uint64_t *bits, size_t n, double *out_re_im);
 
 /* Current qubit layout of the context: phys_of[q] = index bit where circuit qubit q
@@ -238,6 +240,8 @@ int rcs_state_device(rcs_ctx *ctx, void **d_state);
 int rcs_sync(rcs_ctx *ctx);
 
 /* T = sum_i |psi_i|^2, reduced exactly in 2^-62 fixed point and returned as double.
+ * This is the normalisation that the sampler's cumulative distribution (Section 3.2
+ * item 3) and the linear XEB (Section 3.2 item 4, scored in Section 5.1) divide by.
  * Synchronous. */
 int rcs_norm(rcs_ctx *ctx, double *out);
 
@@ -377,8 +381,10 @@ int rcs_batch_run(const rcs_grid *grids, const rcs_gate *const *gates, const siz
  * running while a stream is captured into a CUDA graph, where cudaMalloc is not
  * allowed, or hosts whose device memory comes only from their own arena.)
  *
- * d_state: DEVICE, 2^n_qubits complex64 amplitudes (interleaved re, im);
- * d_samples: DEVICE, count uint64 basis indices; d_out_xeb: DEVICE, one double;
+ * d_state: DEVICE, 2^n_qubits complex64 amplitudes (interleaved re, im), 16-byte
+ * aligned; d_samples: DEVICE, count uint64 basis indices, 8-byte aligned;
+ * d_out_xeb: DEVICE, one double, 8-byte aligned (a misaligned pointer gives
+ * RCS_ERR_ARG before anything is launched);
  * stream: cudaStream_t (0 = legacy default stream). Work is enqueued on the
  * stream and the call returns; an index >= 2^n or an unusable state makes the
  * result NaN.
@@ -388,7 +394,9 @@ int rcs_batch_run(const rcs_grid *grids, const rcs_gate *const *gates, const siz
  * count <= 67108864 (2^26) and 1 <= n_qubits <= 34, else RCS_ERR_ARG with a
  * message for rcs_last_error(NULL). The first call on a device looks up the
  * array's device address (with that device current); make that first call
- * before any stream capture. Every call shares the array: calls whose work
+ * before any stream capture. The address is kept for the process: after a
+ * cudaDeviceReset() of a device, do not call this entry point on that device
+ * again. Devices with ordinals >= 64 get RCS_ERR_UNSUPPORTED. Every call shares the array: calls whose work
  * overlaps on the GPU (other streams, other host threads) race and must be
  * serialised by the caller. */
 int rcs_xeb_static(const void *d_state, int n_qubits, const uint64_t *d_samples, size_t count, double *d_out_xeb,

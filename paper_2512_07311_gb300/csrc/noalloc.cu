@@ -125,7 +125,10 @@ __global__ void __launch_bounds__(kThreads) k_static_final(const uint64_t *__res
 }
 
 std::mutex g_setup_mu;
-void *g_scratch_addr[64] = {};  // device address of g_xeb_scratch, per device
+// Device address of g_xeb_scratch, per device ordinal, looked up once. It stays valid for
+// the life of the device's primary context; a cudaDeviceReset() unloads the module, so a
+// process that resets a device does not call this entry point on it again.
+void *g_scratch_addr[64] = {};
 
 }  // namespace
 
@@ -138,10 +141,19 @@ extern "C" int rcs_xeb_static(const void *d_state, int n_qubits, const uint64_t 
     if (count == 0 || count > uint64_t(kXebParts) * kPerCta)
         return set_thread_error(RCS_ERR_ARG, "rcs_xeb_static: sample count must be 1.." +
                                                  std::to_string(uint64_t(kXebParts) * kPerCta));
+    // the norm kernel reads the state as float4 pairs, the XEB kernels 8-byte words: a
+    // misaligned view (an offset slice of someone else's buffer) is refused here, on the host
+    if (reinterpret_cast<uintptr_t>(d_state) % 16 != 0)
+        return set_thread_error(RCS_ERR_ARG, "rcs_xeb_static: d_state must be 16-byte aligned");
+    if (reinterpret_cast<uintptr_t>(d_samples) % 8 != 0 || reinterpret_cast<uintptr_t>(d_out_xeb) % 8 != 0)
+        return set_thread_error(RCS_ERR_ARG, "rcs_xeb_static: d_samples and d_out_xeb must be 8-byte aligned");
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= 64)
+    if (e != cudaSuccess)
         return set_thread_error(RCS_ERR_CUDA, std::string("rcs_xeb_static: cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dev < 0 || dev >= 64)
+        return set_thread_error(RCS_ERR_UNSUPPORTED,
+                                "rcs_xeb_static: device ordinal " + std::to_string(dev) + " is beyond the 64 this call serves");
     void *scratch;
     {
         std::lock_guard<std::mutex> lock(g_setup_mu);

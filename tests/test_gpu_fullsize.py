@@ -72,8 +72,8 @@ def test_full_size_workload(lib, name, cross):
         a_tc = capi.rcs_amplitudes(ctx, S)
         x_tc = capi.rcs_sample(ctx, shots, seed=11)
         F_tc = capi.rcs_xeb(ctx, x_tc)
-        probe = capi.rcs_amplitudes(ctx, x_tc[:20000])
-        assert (np.abs(probe) > 0).all()
+        probe = capi.rcs_amplitudes(ctx, x_tc)
+        assert (np.abs(probe) > 0).all()  # every shot, not a prefix
         # echo through the tensor-core path
         capi.rcs_apply_circuit(ctx, C.inverse_gates(circ.gates))
         a0 = capi.rcs_amplitudes(ctx, [0])[0]
