@@ -33,6 +33,7 @@ METRIC = "34q 20-cycle circuit time (s), shots/s; fused-TC vs plain FP32 at 1e-5
 # full passes on a 2^27-amplitude state (mean per launch: BF16x3 2.0854 GB, TF32x3 2.0852 GB); the
 # traffic of a pass is proportional to the state size, so a launch at n qubits moves this x 2^n.
 TC_DRAM_BYTES_PER_AMP = {"bf16x3": 2.0854e9 / 2**27, "tf32x3": 2.0852e9 / 2**27}
+PAIR_DRAM_BYTES_PER_AMP = None  # the two-unitary kernel: not yet captured
 WORKLOAD = "34q_5x7m1_20cyc"
 
 
@@ -51,6 +52,8 @@ def parse():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32x3"],
                     help="split precision of the tensor-core passes (bf16x3: the headline path)")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP32 plain/fused comparison runs")
+    ap.add_argument("--pair-passes", action="store_true",
+                    help="time the opt-in two-unitary kernel (RCS_OPT_PAIR_PASSES) as the headline path")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--oracle-check", action="store_true",
                     help="also build the workload's whole state with the CPU oracle (timed: apply, sample, XEB) and "
@@ -394,10 +397,14 @@ def main():
 
     prec = capi.PRECISIONS[args.precision]
     other = "tf32x3" if args.precision == "bf16x3" else "bf16x3"
-    ops_bytes = 65536 if args.precision == "bf16x3" else 98304  # operand image per tensor-core pass
-    ctx = capi.rcs_create(circ.grid, prec, stream=sh)
-    plan = capi.rcs_plan_build(n, circ.gates, prec)
+    flags = capi.RCS_OPT_PAIR_PASSES if args.pair_passes else 0
+    ctx = capi.rcs_create(circ.grid, prec, stream=sh, flags=flags)
+    plan = capi.rcs_plan_build(n, circ.gates, prec, flags=flags)
     info = capi.rcs_plan_info(plan)
+    pairs = int(info["pair_passes"])
+    # operand images uploaded per tensor-core pass: the single-pass image, plus the pair
+    # kernel's complex-form image when the plan pairs passes
+    ops_bytes = (65536 if args.precision == "bf16x3" else 98304) + (32768 if pairs else 0)
     capi.rcs_plan_upload(ctx, plan)
     d_bits = torch.empty(shots, dtype=torch.int64, device="cuda")
     d_xeb = torch.empty(1, dtype=torch.float64, device="cuda")
@@ -466,13 +473,16 @@ def main():
     stages = int(info["prefix_stages"])
     fused = prefix > 0 and full_passes == passes - prefix - 1
     setup = 1 + max(stages - 1, 0) + (0 if (prefix == 0 or fused) else 1)
-    gpu_launches = passes + setup + 1 + 3 + 6 + 2
+    gpu_launches = (passes - pairs) + setup + 1 + 3 + 6 + 2
     bytes_per_launch = 16.0 * 2.0**n
     achieved = bytes_per_launch / t_pass_s / 1e9
+    # traffic: DRAM bytes per launch from an ncu capture of the same kernel (None for a kernel
+    # not captured since it last changed)
+    traffic = PAIR_DRAM_BYTES_PER_AMP if pairs else TC_DRAM_BYTES_PER_AMP[args.precision]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": TC_DRAM_BYTES_PER_AMP[args.precision] * 2.0**n,
-                "traffic_src": "ncu capture at 27 qubits scaled by 2^(n-27)",
-                "kernel": "k_fused_tc", "peak_src": peaks["src"],
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic * 2.0**n if traffic else None,
+                "traffic_src": "ncu capture at 27 qubits scaled by 2^(n-27)" if traffic else None,
+                "kernel": "k_pair_tc (two unitaries per launch)" if pairs else "k_fused_tc", "peak_src": peaks["src"],
                 "algorithmic_bytes_per_launch": bytes_per_launch, "launches_per_step": full_passes,
                 "mean_launch_ms": t_pass_s * 1e3}
 
@@ -499,9 +509,13 @@ def main():
         capi.rcs_reset(ctx)
         capi.rcs_plan_run(ctx, plan)
         amps = {args.precision: capi.rcs_amplitudes(ctx, subset)}
-        for name, p2prec, kmax in (("fp32_plain", capi.RCS_PREC_FP32_PLAIN, 0),
-                                   ("fp32_fused_k4", capi.RCS_PREC_FP32_FUSED, 4), (other, capi.PRECISIONS[other], 0)):
-            p2 = capi.rcs_plan_build(n, circ.gates, p2prec, kmax)
+        arms = [("fp32_plain", capi.RCS_PREC_FP32_PLAIN, 0, 0), ("fp32_fused_k4", capi.RCS_PREC_FP32_FUSED, 4, 0),
+                (other, capi.PRECISIONS[other], 0, 0)]
+        if args.precision == "bf16x3":
+            # the opt-in two-unitary round trips, timed beside the default single passes
+            arms.append(("bf16x3_pair_passes", prec, 0, 0 if pairs else capi.RCS_OPT_PAIR_PASSES))
+        for name, p2prec, kmax, flags in arms:
+            p2 = capi.rcs_plan_build(n, circ.gates, p2prec, kmax, flags=flags)
             i2 = capi.rcs_plan_info(p2)
             capi.rcs_plan_upload(ctx, p2)
             capi.rcs_reset(ctx)
@@ -523,7 +537,7 @@ def main():
 
         ref = amps["fp32_fused_k4"]
         compare["subset_infidelity_vs_fp32_fused_k4"] = {k: subset_infidelity(amps[k], ref)
-                                                         for k in ("bf16x3", "tf32x3", "fp32_plain")}
+                                                         for k in amps if k != "fp32_fused_k4"}
         compare[f"{args.precision}_apply_s"] = statistics.median(apply_ms) / 1e3
         compare["speedup_vs_fp32_plain"] = compare["fp32_plain"]["apply_s"] / compare[f"{args.precision}_apply_s"]
 

@@ -92,14 +92,25 @@ typedef struct {
  * k_max in 2..5 minimising (passes at width k) x (measured time of a width-k pass
  * on this state), by timed trial passes on the first call for this qubit count on
  * this device (cached for the process; the trials leave the state bit-identical).
- * stream: cudaStream_t for all device work. */
+ * flags: RCS_OPT_* bits (0 = defaults). stream: cudaStream_t for all device work. */
 typedef struct {
     int32_t precision;
     int32_t k_max;
     int32_t autotune;
-    int32_t reserved;
+    int32_t flags;
     uint64_t stream;
 } rcs_opts;
+
+/* Opt-in for BF16X3 plans on 13 or more qubits: apply two consecutive 6-qubit passes in
+ * one round trip of the state through HBM (the pair kernel: each 2^13-amplitude tile is
+ * read once, both unitaries are applied on the tensor cores, and it is written once).
+ * The arithmetic of each unitary is the same as in a single pass (BF16 hi/lo split of
+ * the FP32 input, three products, FP32 accumulation); only the order of the FP32
+ * accumulation differs. Off by default: on GB300 a pair launch currently takes longer
+ * than the two single passes it replaces (its regrouping step and tensor-memory
+ * traffic lengthen the per-tile pipeline), so the default plans keep one round trip
+ * per pass. */
+#define RCS_OPT_PAIR_PASSES 1
 
 /* Description of a built plan (rcs_plan_info). */
 typedef struct {
@@ -108,7 +119,7 @@ typedef struct {
     int64_t n_gates;
     int64_t n_passes;
     int32_t k_max;        /* largest block width used */
-    int32_t reserved;
+    int32_t pair_passes;  /* two-unitary round trips of a run from |0...0> (RCS_OPT_PAIR_PASSES) */
     double hbm_bytes;     /* algorithmic HBM bytes: 16 * 2^n per pass */
     double flops;         /* algorithmic real flops of all passes (x3 for the split-precision path) */
     int64_t prefix_passes; /* leading passes a run from |0...0> does on compact sub-states (0: none) */
@@ -116,8 +127,9 @@ typedef struct {
     int32_t prefix_stages; /* sub-states, nested and growing, each expanded into the next; the first
                               full pass reads the last one directly where its kernel allows, else it
                               is expanded into the full state */
-    double zero_hbm_bytes; /* algorithmic HBM bytes of rcs_plan_run from |0...0>: each pass at the size
-                              of the state it runs on, the zero fill, the expansions */
+    double zero_hbm_bytes; /* algorithmic HBM bytes of rcs_plan_run from |0...0>: each round trip (a
+                              pass, or a pair of passes) at the size of the state it runs on, the zero
+                              fill, the expansions */
 } rcs_plan_stats;
 
 /* ------------------------------------------------------------------ context */
@@ -174,6 +186,16 @@ int rcs_apply_circuit(rcs_ctx *ctx, const rcs_gate *gates, size_t n_gates);
  * else RCS_ERR_UNSUPPORTED. Asynchronous. */
 int rcs_apply_unitary(rcs_ctx *ctx, int k, const int32_t *targets, const double *u_re_im);
 
+/* Applies count dense unitaries in order (psi <- U_{count-1} ... U_0 psi), each as
+ * rcs_apply_unitary would: unitary i has k[i] targets (1..6), listed in targets at
+ * offset k[0] + ... + k[i-1], and its 2^k x 2^k complex128 matrix (row-major,
+ * interleaved) at u_re_im[i]. All are validated before anything runs (a rejected
+ * list leaves the state unchanged). With BF16X3 on n >= 13 qubits and
+ * RCS_OPT_PAIR_PASSES in the context's flags, consecutive 6-qubit unitaries share one
+ * round trip of the state (the pair kernel). Asynchronous. */
+int rcs_apply_unitaries(rcs_ctx *ctx, size_t count, const int32_t *k, const int32_t *targets,
+                        const double *const *u_re_im);
+
 /* Host-only planning (no GPU needed): fuses the gates into passes for an n-qubit
  * state with the given options (NULL = FP32_FUSED, k_max 4). The plan keeps its
  * own copy of everything it needs. */
@@ -195,8 +217,9 @@ int rcs_plan_pass(const rcs_plan *plan, size_t i, int32_t *k, int32_t *targets, 
 
 /* Device time (ms) of the full-state passes of the last rcs_apply_circuit or
  * rcs_plan_run on this context (CUDA events around them on the context's stream;
- * the sub-state prefix and expansion are not included), and how many there were.
- * Waits for those passes to finish. */
+ * the sub-state prefix and expansion are not included), and how many kernel
+ * launches they took (a two-unitary round trip is one launch). Waits for those
+ * passes to finish. */
 int rcs_last_pass_timing(rcs_ctx *ctx, float *ms, int64_t *full_passes);
 
 /* Uploads the plan's pass table and matrices to the device of ctx (once per plan

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "librcs.so")
 RCS_OK = 0
 RCS_ERR_ARG, RCS_ERR_QUBIT, RCS_ERR_OOM, RCS_ERR_CUDA, RCS_ERR_TIMEOUT, RCS_ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
 RCS_PREC_FP32_PLAIN, RCS_PREC_FP32_FUSED, RCS_PREC_BF16X3, RCS_PREC_TF32X3 = 0, 1, 2, 3
+RCS_OPT_PAIR_PASSES = 1  # opt-in: consecutive BF16x3 passes share one round trip (the pair kernel)
 PRECISIONS = {"fp32_plain": RCS_PREC_FP32_PLAIN, "fp32_fused": RCS_PREC_FP32_FUSED, "bf16x3": RCS_PREC_BF16X3,
               "tf32x3": RCS_PREC_TF32X3}
 
@@ -37,12 +38,12 @@ class rcs_grid(ctypes.Structure):
 
 class rcs_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("k_max", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("stream", ctypes.c_uint64)]
+                ("flags", ctypes.c_int32), ("stream", ctypes.c_uint64)]
 
 
 class rcs_plan_stats(ctypes.Structure):
     _fields_ = [("n_qubits", ctypes.c_int32), ("precision", ctypes.c_int32), ("n_gates", ctypes.c_int64),
-                ("n_passes", ctypes.c_int64), ("k_max", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("n_passes", ctypes.c_int64), ("k_max", ctypes.c_int32), ("pair_passes", ctypes.c_int32),
                 ("hbm_bytes", ctypes.c_double), ("flops", ctypes.c_double), ("prefix_passes", ctypes.c_int64),
                 ("prefix_qubits", ctypes.c_int32), ("prefix_stages", ctypes.c_int32),
                 ("zero_hbm_bytes", ctypes.c_double)]
@@ -69,6 +70,7 @@ SIGNATURES = [
     ("rcs_reset", ctypes.c_int, [_P]),
     ("rcs_apply_circuit", ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     ("rcs_apply_unitary", ctypes.c_int, [_P, ctypes.c_int, _i32p, _f64p]),
+    ("rcs_apply_unitaries", ctypes.c_int, [_P, ctypes.c_size_t, _i32p, _i32p, ctypes.POINTER(_f64p)]),
     ("rcs_plan_build", ctypes.c_int, [ctypes.c_int, _P, ctypes.c_size_t, ctypes.POINTER(rcs_opts), ctypes.POINTER(_P)]),
     ("rcs_plan_info", ctypes.c_int, [_P, ctypes.POINTER(rcs_plan_stats)]),
     ("rcs_plan_layout", ctypes.c_int, [_P, _i32p]),
@@ -149,17 +151,18 @@ def _gates_ptr(gates: np.ndarray, umats: dict | None):
     return (g.ctypes.data if len(g) else None), keep
 
 
-def _opts(precision: int, k_max: int, stream: int, autotune: int = 0):
+def _opts(precision: int, k_max: int, stream: int, autotune: int = 0, flags: int = 0):
     o = rcs_opts()
     o.precision = precision
     o.k_max = k_max
     o.autotune = autotune
+    o.flags = flags
     o.stream = stream
     return o
 
 
 def rcs_create(n_or_grid, precision: int = RCS_PREC_FP32_FUSED, k_max: int = 0, stream: int = 0,
-               autotune: int = 0):
+               autotune: int = 0, flags: int = 0):
     """n_or_grid: a qubit count (1 x n grid) or a circuits.Grid."""
     L = load()
     g = rcs_grid()
@@ -170,7 +173,7 @@ def rcs_create(n_or_grid, precision: int = RCS_PREC_FP32_FUSED, k_max: int = 0, 
         rem = np.ascontiguousarray(n_or_grid.removed, dtype=np.int32)
         g.n_removed = len(rem)
         g.removed = rem.ctypes.data_as(_i32p) if len(rem) else None
-    o = _opts(precision, k_max, stream, autotune)
+    o = _opts(precision, k_max, stream, autotune, flags)
     out = _P()
     _check(L.rcs_create(ctypes.byref(g), ctypes.byref(o), ctypes.byref(out)))
     return out
@@ -203,10 +206,23 @@ def rcs_apply_unitary(ctx, targets, u: np.ndarray):
     _check(load().rcs_apply_unitary(ctx, len(t), t.ctypes.data_as(_i32p), m.ctypes.data_as(_f64p)), ctx)
 
 
+def rcs_apply_unitaries(ctx, items):
+    """items: sequence of (targets, u) applied in order (consecutive 6-qubit ones share a
+    round trip of the state under BF16X3 when the context has RCS_OPT_PAIR_PASSES)."""
+    items = list(items)
+    ks = np.array([len(t) for t, _ in items], dtype=np.int32)
+    tg = np.ascontiguousarray(np.concatenate([np.asarray(t, dtype=np.int32) for t, _ in items]) if items
+                              else np.zeros(0, dtype=np.int32))
+    mats = [np.ascontiguousarray(np.asarray(u, dtype=np.complex128).reshape(-1)).view(np.float64) for _, u in items]
+    ptrs = (_f64p * max(1, len(mats)))(*[m.ctypes.data_as(_f64p) for m in mats])
+    _check(load().rcs_apply_unitaries(ctx, len(items), ks.ctypes.data_as(_i32p), tg.ctypes.data_as(_i32p), ptrs),
+           ctx)
+
+
 def rcs_plan_build(n: int, gates: np.ndarray, precision: int = RCS_PREC_FP32_FUSED, k_max: int = 0,
-                   umats: dict | None = None):
+                   umats: dict | None = None, flags: int = 0):
     ptr, keep = _gates_ptr(gates, umats)
-    o = _opts(precision, k_max, 0)
+    o = _opts(precision, k_max, 0, 0, flags)
     out = _P()
     _check(load().rcs_plan_build(n, ptr, len(keep[0]), ctypes.byref(o), ctypes.byref(out)))
     return out

@@ -211,6 +211,7 @@ int build_plan(rcs_ctx *ctx, int n, const std::vector<HostGate> &hg, const rcs_o
                bool allow_layout) {
     plan->n = n;
     plan->precision = o.precision;
+    plan->pairs = o.precision == RCS_PREC_BF16X3 && (o.flags & RCS_OPT_PAIR_PASSES);
     plan->n_gates = int64_t(hg.size());
     plan->phys_of.clear();
     plan->stage_spans.clear();
@@ -329,10 +330,20 @@ void build_ops_images(Plan &plan, std::vector<uint8_t> *img) {
     size_t count = 0;
     for (size_t i = 0; i < plan.passes.size(); ++i)
         if (plan.passes[i].kind == PASS_TC) plan.tc_offset[i] = int64_t(per * count++);
-    img->assign(per * count, 0);
+    // the pair kernel's images (complex block form) follow the single-pass ones
+    plan.pair_offset.assign(plan.passes.size(), -1);
+    size_t total = per * count;
+    if (plan.pairs)
+        for (size_t i = 0; i < plan.passes.size(); ++i)
+            if (plan.passes[i].kind == PASS_TC) {
+                plan.pair_offset[i] = int64_t(total);
+                total += pair_ops_bytes();
+            }
+    img->assign(total, 0);
     // independent images in disjoint slices of the buffer
     host_parallel_for(plan.passes.size(), [&](size_t i) {
         if (plan.tc_offset[i] >= 0) tc_build_ops(plan.passes[i], img->data() + plan.tc_offset[i], tf32);
+        if (plan.pair_offset[i] >= 0) pair_build_ops(plan.passes[i], img->data() + plan.pair_offset[i]);
     });
 }
 
@@ -385,14 +396,12 @@ int run_passes(rcs_ctx *c, const Plan &plan, const uint8_t *d_ops, bool from_zer
         return rc;
     }
     cudaEventRecord(c->ev_full[0], c->stream);
-    for (size_t i = first; i < plan.passes.size(); ++i) {
-        const Pass &p = plan.passes[i];
-        const uint8_t *ops = p.kind == PASS_TC ? d_ops + plan.tc_offset[i] : nullptr;
-        if (launch_one(c, c->psi, c->n, p, ops, plan_tf32(plan)) != RCS_OK)
-            return fail(c, RCS_ERR_CUDA, "launch of pass " + std::to_string(i) + " failed: " + take_launch_error());
-    }
+    int64_t launches = 0;
+    if (launch_pass_range(plan, c->psi, c->n, first, plan.passes.size(), 0, d_ops, c->d_err, c->stream, &launches) !=
+        RCS_OK)
+        return fail(c, RCS_ERR_CUDA, "launch of a full-state pass failed: " + take_launch_error());
     cudaEventRecord(c->ev_full[1], c->stream);
-    c->timed_passes = int64_t(plan.passes.size() - first);
+    c->timed_passes = launches;
     c->sums_valid = false;
     return RCS_OK;
 }
@@ -475,11 +484,10 @@ int run_substages(const Plan &plan, const std::vector<SubStage> &stages, void *p
                 }
             if (launch_expand(next, m, cur, inner, stream) != RCS_OK) return RCS_ERR_CUDA;
         }
-        for (int i = st.first; i < st.first + st.count; ++i) {
-            const Pass q = compact_pass(plan.passes[size_t(i)], st.tmask);
-            const uint8_t *ops = q.kind == PASS_TC ? d_ops + plan.tc_offset[size_t(i)] : nullptr;
-            if (launch_plan_pass(next, m, q, ops, d_err, stream, tf32) != RCS_OK) return RCS_ERR_CUDA;
-        }
+        int64_t launches = 0;
+        if (launch_pass_range(plan, next, m, size_t(st.first), size_t(st.first + st.count), st.tmask, d_ops, d_err,
+                              stream, &launches) != RCS_OK)
+            return RCS_ERR_CUDA;
         cur = next;
         cur_mask = st.tmask;
     }
@@ -491,6 +499,39 @@ int run_substages(const Plan &plan, const std::vector<SubStage> &stages, void *p
         return rc;
     }
     return launch_expand(psi, plan.n, cur, cur_mask, stream);
+}
+
+bool plan_pairs_at(const Plan &plan, size_t i, size_t end, int n) {
+    return plan.pairs && i + 1 < end && pair_fits(plan.passes[i], plan.passes[i + 1], n);
+}
+
+int launch_pass_range(const Plan &plan, void *psi, int n, size_t first, size_t end, uint64_t T, const uint8_t *d_ops,
+                      int *d_err, void *stream, int64_t *launches) {
+    const bool tf32 = plan_tf32(plan);
+    Pass c0, c1;  // targets renumbered into the sub-state
+    auto at = [&](size_t i, Pass &tmp) -> const Pass & {
+        if (!T) return plan.passes[i];
+        tmp = compact_pass(plan.passes[i], T);
+        return tmp;
+    };
+    for (size_t i = first; i < end;) {
+        const Pass &p = at(i, c0);
+        if (plan_pairs_at(plan, i, end, n) && plan.pair_offset.size() == plan.passes.size() &&
+            plan.pair_offset[i] >= 0 && plan.pair_offset[i + 1] >= 0) {
+            const Pass &p2 = at(i + 1, c1);
+            if (launch_pair_tc(psi, n, p, p2, d_ops + plan.pair_offset[i], d_ops + plan.pair_offset[i + 1], d_err,
+                               stream) != RCS_OK)
+                return RCS_ERR_CUDA;
+            ++*launches;
+            i += 2;
+            continue;
+        }
+        const uint8_t *ops = p.kind == PASS_TC ? d_ops + plan.tc_offset[i] : nullptr;
+        if (launch_plan_pass(psi, n, p, ops, d_err, stream, tf32) != RCS_OK) return RCS_ERR_CUDA;
+        ++*launches;
+        ++i;
+    }
+    return RCS_OK;
 }
 
 BitMap plan_to_stored(const Plan &plan) {
@@ -689,9 +730,10 @@ int rcs_apply_circuit(rcs_ctx *c, const rcs_gate *gates, size_t n_gates) {
     RCS_CATCH(c)
 }
 
-int rcs_apply_unitary(rcs_ctx *c, int k, const int32_t *targets, const double *u_re_im) {
-    if (!c) return fail(nullptr, RCS_ERR_ARG, "null context");
-    RCS_TRY(c)
+namespace {
+// One caller unitary as a pass on the context's stored qubits: validated (targets,
+// unitarity to 1e-6), reordered to ascending targets, and given the kernel kind.
+int unitary_pass(rcs_ctx *c, int k, const int32_t *targets, const double *u_re_im, Pass *out) {
     if (k < 1 || k > kTcK || !targets || !u_re_im) return fail(c, RCS_ERR_ARG, "k must be 1..6 with targets and u");
     if (k > c->n) return fail(c, RCS_ERR_QUBIT, "more targets than qubits");
     uint64_t seen = 0;
@@ -700,11 +742,8 @@ int rcs_apply_unitary(rcs_ctx *c, int k, const int32_t *targets, const double *u
             return fail(c, RCS_ERR_QUBIT, "bad or repeated target");
         seen |= 1ull << targets[i];
     }
-    if (c->fresh) set_identity_layout(c);
-    if (int rc = materialize(c); rc != RCS_OK) return rc;
     int tg[8];
     for (int i = 0; i < k; ++i) tg[i] = c->phys_of[targets[i]];  // stored positions
-    targets = tg;
     const int d = 1 << k;
     std::vector<cd> U(size_t(d) * d);
     for (size_t e = 0; e < U.size(); ++e) U[e] = cd(u_re_im[2 * e], u_re_im[2 * e + 1]);
@@ -716,10 +755,10 @@ int rcs_apply_unitary(rcs_ctx *c, int k, const int32_t *targets, const double *u
             worst = std::max(worst, std::abs(s - (r == cc ? 1.0 : 0.0)));
         }
     if (!(worst <= 1e-6)) return fail(c, RCS_ERR_ARG, "matrix is not unitary to 1e-6");
-    // reorder to ascending targets: local bit i (targets[i]) moves to its rank
+    // reorder to ascending targets: local bit i (tg[i]) moves to its rank
     int order[8], rank[8];
     for (int i = 0; i < k; ++i) order[i] = i;
-    std::sort(order, order + k, [&](int x, int y) { return targets[x] < targets[y]; });
+    std::sort(order, order + k, [&](int x, int y) { return tg[x] < tg[y]; });
     for (int p = 0; p < k; ++p) rank[order[p]] = p;
     auto remap = [&](int j) {
         int r = 0;
@@ -727,21 +766,46 @@ int rcs_apply_unitary(rcs_ctx *c, int k, const int32_t *targets, const double *u
             if ((j >> i) & 1) r |= 1 << rank[i];
         return r;
     };
-    Pass p;
+    Pass &p = *out;
     p.k = k;
-    for (int i = 0; i < 8; ++i) p.t[i] = i < k ? targets[order[i]] : -1;
+    for (int i = 0; i < 8; ++i) p.t[i] = i < k ? tg[order[i]] : -1;
     p.U.assign(U.size(), cd(0.0));
     for (int j = 0; j < d; ++j)
         for (int l = 0; l < d; ++l) p.U[size_t(remap(j)) * d + remap(l)] = U[size_t(j) * d + l];
-    Plan plan;
-    plan.n = c->n;
-    plan.precision = c->opts.precision;
-    plan.n_gates = 1;
     const bool tc_prec = c->opts.precision == RCS_PREC_BF16X3 || c->opts.precision == RCS_PREC_TF32X3;
     if (k == kTcK && tc_prec && c->n >= kTcK + 7) p.kind = PASS_TC;
     else if (k <= 5) p.kind = PASS_SIMT;
     else return fail(c, RCS_ERR_UNSUPPORTED, "6-qubit unitaries need a tensor-core precision and n >= 13");
-    plan.passes.push_back(p);
+    return RCS_OK;
+}
+}  // namespace
+
+int rcs_apply_unitary(rcs_ctx *c, int k, const int32_t *targets, const double *u_re_im) {
+    if (!c) return fail(nullptr, RCS_ERR_ARG, "null context");
+    const double *u[1] = {u_re_im};
+    return rcs_apply_unitaries(c, 1, &k, targets, u);
+}
+
+int rcs_apply_unitaries(rcs_ctx *c, size_t count, const int32_t *k, const int32_t *targets,
+                        const double *const *u_re_im) {
+    if (!c) return fail(nullptr, RCS_ERR_ARG, "null context");
+    RCS_TRY(c)
+    if (count == 0) return RCS_OK;
+    if (!k || !targets || !u_re_im) return fail(c, RCS_ERR_ARG, "null argument");
+    if (c->fresh) set_identity_layout(c);
+    Plan plan;
+    plan.n = c->n;
+    plan.precision = c->opts.precision;
+    plan.pairs = c->opts.precision == RCS_PREC_BF16X3 && (c->opts.flags & RCS_OPT_PAIR_PASSES);
+    plan.n_gates = int64_t(count);
+    plan.passes.resize(count);
+    size_t off = 0;
+    for (size_t i = 0; i < count; ++i) {
+        if (k[i] < 1 || k[i] > kTcK) return fail(c, RCS_ERR_ARG, "k must be 1..6 with targets and u");
+        if (int rc = unitary_pass(c, k[i], targets + off, u_re_im[i], &plan.passes[i]); rc != RCS_OK) return rc;
+        off += size_t(k[i]);
+    }
+    if (int rc = materialize(c); rc != RCS_OK) return rc;
     std::vector<uint8_t> img;
     build_ops_images(plan, &img);
     if (!img.empty()) {
@@ -805,25 +869,42 @@ int rcs_plan_info(const rcs_plan *plan, rcs_plan_stats *out) {
     out->prefix_passes = plan_stages(p, &stages);
     out->prefix_qubits = stages.empty() ? 0 : std::popcount(stages.back().tmask);
     out->prefix_stages = int32_t(stages.size());
+    // round trips of passes [first, end) on a 2^m state, counting the two-unitary ones
+    int32_t pairs = 0;
+    auto trips = [&](size_t first, size_t end, int m) {
+        double t = 0;
+        for (size_t i = first; i < end; ++t) {
+            if (plan_pairs_at(p, i, end, m)) {
+                ++pairs;
+                i += 2;
+            } else {
+                ++i;
+            }
+        }
+        return t;
+    };
     // what run_substages and the passes after it move, from |0...0>
     if (stages.empty()) {
-        out->zero_hbm_bytes = 8.0 * amps + out->hbm_bytes;  // zero fill, then every pass on the full state
+        // zero fill, then every round trip on the full state
+        out->zero_hbm_bytes = 8.0 * amps + 16.0 * amps * trips(0, p.passes.size(), p.n);
     } else {
         double z = 8.0 * std::ldexp(1.0, std::popcount(stages.front().tmask));  // first sub-state's zero fill
         for (size_t si = 0; si < stages.size(); ++si) {
-            const double m = std::ldexp(1.0, std::popcount(stages[si].tmask));
-            z += 16.0 * m * double(stages[si].count);
+            const int mb = std::popcount(stages[si].tmask);
+            const double m = std::ldexp(1.0, mb);
+            z += 16.0 * m * trips(size_t(stages[si].first), size_t(stages[si].first + stages[si].count), mb);
             if (si + 1 < stages.size()) z += 8.0 * m + 8.0 * std::ldexp(1.0, std::popcount(stages[si + 1].tmask));
         }
         // the last sub-state is read once into the full state: by the first full pass itself or by an
-        // expansion before it; either way 8 * 2^m in and 8 * 2^n out, plus 16 * 2^n per other full pass
+        // expansion before it; either way 8 * 2^m in and 8 * 2^n out, plus 16 * 2^n per other round trip
         const size_t after = size_t(out->prefix_passes);
         const double mlast = std::ldexp(1.0, std::popcount(stages.back().tmask));
         const bool fused = after < p.passes.size() && tc_pass_takes_substate(p.passes[after], p.n);
         z += 8.0 * mlast + 8.0 * amps;
-        z += 16.0 * amps * double(p.passes.size() - after - (fused ? 1 : 0));
+        z += 16.0 * amps * trips(after + (fused ? 1 : 0), p.passes.size(), p.n);
         out->zero_hbm_bytes = z;
     }
+    out->pair_passes = pairs;
     return RCS_OK;
 }
 

@@ -497,13 +497,10 @@ int record_chain(rcs_batch *b, InstHost &h, cudaStream_t st) {
     } else if ((rc = launch_init_zero(h.psi, h.n, st)) != RCS_OK) {
         return bfail(b, rc, "reset: " + take_launch_error());
     }
-    const bool tf32 = h.plan.precision == RCS_PREC_TF32X3;
-    for (size_t i = first; i < h.plan.passes.size(); ++i) {
-        const Pass &p = h.plan.passes[i];
-        const uint8_t *ops = p.kind == PASS_TC ? h.d_ops + h.plan.tc_offset[i] : nullptr;
-        if ((rc = launch_plan_pass(h.psi, h.n, p, ops, b->d_err, st, tf32)) != RCS_OK)
-            return bfail(b, rc, "pass launch: " + take_launch_error());
-    }
+    int64_t launches = 0;
+    if ((rc = launch_pass_range(h.plan, h.psi, h.n, first, h.plan.passes.size(), 0, h.d_ops, b->d_err, st,
+                                &launches)) != RCS_OK)
+        return bfail(b, rc, "pass launch: " + take_launch_error());
     return launch_sampling(b, h, st);
 }
 
@@ -641,6 +638,7 @@ int rcs_batch_create(const rcs_batch_item *items, size_t n_items, const rcs_opts
         if (b->tc) {
             rcs_opts o{};
             o.precision = opts->precision;
+            o.flags = opts->flags;
             for (size_t i = 0; i < n_items; ++i) {
                 InstHost &h = b->inst[i];
                 std::vector<uint8_t> img;

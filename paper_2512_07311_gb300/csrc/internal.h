@@ -61,10 +61,12 @@ struct Plan {
     int64_t n_gates = 0;
     std::vector<Pass> passes;
     std::vector<int> stage_spans;  // sub-state widths of a run from |0...0> (empty: one of n - 4)
+    bool pairs = false;  // consecutive tensor-core passes run as one two-unitary round trip (BF16X3)
     // device copies, per context device (uploaded lazily)
     int dev = -1;
     void *d_tc_ops = nullptr;   // hi/lo operand images of PASS_TC passes
     std::vector<int64_t> tc_offset;  // byte offset of each pass's image (-1 if none)
+    std::vector<int64_t> pair_offset;  // byte offset of each pass's pair-kernel image (-1 if none)
 };
 
 // Fuses gates into passes. k_max: largest block; pad_to: 0, or a width every
@@ -155,6 +157,22 @@ int launch_pass_tc_from_sub(void *psi, int n, const Pass &p, const void *d_ops, 
 // 96 KB), and its builder.
 size_t tc_ops_bytes(bool tf32);
 void tc_build_ops(const Pass &p, void *host_image, bool tf32);
+
+// Two consecutive 6-qubit passes in one round trip of a 2^n state (k_pair.cu, BF16x3):
+// whether two passes can run this way, the size and builder of one pass's image for
+// it (48 KB, complex block form), and the launcher.
+bool pair_fits(const Pass &p1, const Pass &p2, int n);
+size_t pair_ops_bytes();
+void pair_build_ops(const Pass &p, void *host_image);
+int launch_pair_tc(void *psi, int n, const Pass &p1, const Pass &p2, const void *d_ops1, const void *d_ops2, int *d_err,
+                   void *stream);
+// Whether passes i and i+1 (< end) of a plan run as one two-unitary round trip.
+bool plan_pairs_at(const Plan &plan, size_t i, size_t end, int n);
+// Launches passes [first, end) of a plan on the 2^n-amplitude state psi, their targets
+// renumbered into the sub-state of mask T when T != 0; consecutive tensor-core passes
+// share a round trip where plan_pairs_at says so. *launches counts kernel launches.
+int launch_pass_range(const Plan &plan, void *psi, int n, size_t first, size_t end, uint64_t T, const uint8_t *d_ops,
+                      int *d_err, void *stream, int64_t *launches);
 
 // Sampler / readout (k_sample.cu)
 // to_stored: caller basis index -> stored index (the state's qubit layout). Blocks are

@@ -180,6 +180,7 @@ def test_zero_state_byte_count():
         info, passes = _plan_passes(plan)
     finally:
         capi.rcs_plan_destroy(plan)
+    assert info["pair_passes"] == 0
     pre = info["prefix_passes"]
     assert pre > 0 and info["prefix_stages"] >= 1
     # the union of targets after each prefix pass: no stage is narrower than the union of the
@@ -197,3 +198,16 @@ def test_zero_state_byte_count():
     full = 16.0 * 2**n * (info["n_passes"] - pre - 1)  # the first full pass reads the sub-state
     assert lo + full <= info["zero_hbm_bytes"] <= hi + full
     assert info["zero_hbm_bytes"] < info["hbm_bytes"]
+    # the same plan with two-unitary round trips (opt-in): the same passes; every pair saves
+    # one round trip of the state it runs on, and the full-state passes after the first pair
+    # up in order
+    plan = capi.rcs_plan_build(n, circ.gates, capi.RCS_PREC_BF16X3, flags=capi.RCS_OPT_PAIR_PASSES)
+    try:
+        info2, passes2 = _plan_passes(plan)
+    finally:
+        capi.rcs_plan_destroy(plan)
+    assert [tuple(t) for t, _ in passes2] == [tuple(t) for t, _ in passes]
+    n_full = info["n_passes"] - pre - 1
+    saved = info["zero_hbm_bytes"] - info2["zero_hbm_bytes"]
+    assert n_full // 2 <= info2["pair_passes"] <= info["n_passes"] // 2
+    assert 16.0 * 2**n * (n_full // 2) <= saved <= 16.0 * 2**n * info2["pair_passes"]
