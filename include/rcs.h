@@ -262,6 +262,17 @@ int rcs_state_device(rcs_ctx *ctx, void **d_state);
  * RCS_ERR_ARG for an out-of-range bitstring or an unusable state), then clears them. */
 int rcs_sync(rcs_ctx *ctx);
 
+/* Test hook for the bounded waits of the tensor-core kernels (single passes and pair
+ * passes), process-wide: while skip_tile >= 0, every tensor-core launch has its first CTA
+ * skip the MMAs of its tile number skip_tile (it issues and commits nothing for that
+ * tile), so the waits for that tile run out after wait_limit_s seconds of SM clock; the
+ * kernel then stops, waits for its own MMAs and copies in flight, frees its tensor memory
+ * and raises the error that rcs_sync reports as RCS_ERR_TIMEOUT (the state is then
+ * partly updated). skip_tile = -1 restores normal operation; wait_limit_s <= 0 restores
+ * the default limit (about one second). The limit converts to cycles at the current
+ * device's clock rate. No GPU fault is involved. */
+int rcs_tc_test_fault(int64_t skip_tile, double wait_limit_s);
+
 /* T = sum_i |psi_i|^2, reduced exactly in 2^-62 fixed point and returned as double.
  * This is the normalisation that the sampler's cumulative distribution (Section 3.2
  * item 3) and the linear XEB (Section 3.2 item 4, scored in Section 5.1) divide by.

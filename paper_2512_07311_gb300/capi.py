@@ -71,6 +71,7 @@ SIGNATURES = [
     ("rcs_apply_circuit", ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     ("rcs_apply_unitary", ctypes.c_int, [_P, ctypes.c_int, _i32p, _f64p]),
     ("rcs_apply_unitaries", ctypes.c_int, [_P, ctypes.c_size_t, _i32p, _i32p, ctypes.POINTER(_f64p)]),
+    ("rcs_tc_test_fault", ctypes.c_int, [ctypes.c_int64, ctypes.c_double]),
     ("rcs_plan_build", ctypes.c_int, [ctypes.c_int, _P, ctypes.c_size_t, ctypes.POINTER(rcs_opts), ctypes.POINTER(_P)]),
     ("rcs_plan_info", ctypes.c_int, [_P, ctypes.POINTER(rcs_plan_stats)]),
     ("rcs_plan_layout", ctypes.c_int, [_P, _i32p]),
@@ -217,6 +218,11 @@ def rcs_apply_unitaries(ctx, items):
     ptrs = (_f64p * max(1, len(mats)))(*[m.ctypes.data_as(_f64p) for m in mats])
     _check(load().rcs_apply_unitaries(ctx, len(items), ks.ctypes.data_as(_i32p), tg.ctypes.data_as(_i32p), ptrs),
            ctx)
+
+
+def rcs_tc_test_fault(skip_tile: int, wait_limit_s: float = 0.0):
+    """Test hook of the tensor-core kernels' bounded waits (see include/rcs.h)."""
+    _check(load().rcs_tc_test_fault(skip_tile, wait_limit_s))
 
 
 def rcs_plan_build(n: int, gates: np.ndarray, precision: int = RCS_PREC_FP32_FUSED, k_max: int = 0,

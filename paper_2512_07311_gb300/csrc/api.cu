@@ -780,6 +780,21 @@ int unitary_pass(rcs_ctx *c, int k, const int32_t *targets, const double *u_re_i
 }
 }  // namespace
 
+int rcs_tc_test_fault(int64_t skip_tile, double wait_limit_s) {
+    if (skip_tile > (int64_t(1) << 30)) return fail(nullptr, RCS_ERR_ARG, "skip_tile out of range");
+    long long cycles = 0;
+    if (wait_limit_s > 0) {
+        if (!(wait_limit_s <= 100.0)) return fail(nullptr, RCS_ERR_ARG, "wait limit must be at most 100 s");
+        int dev = 0, khz = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess ||
+            khz <= 0)
+            khz = 2070000;  // the GB300 maximum SM clock
+        cycles = std::max(1000ll, (long long)(wait_limit_s * double(khz) * 1e3));
+    }
+    tc_set_test_fault(skip_tile < 0 ? -1 : int(skip_tile), cycles);
+    return RCS_OK;
+}
+
 int rcs_apply_unitary(rcs_ctx *c, int k, const int32_t *targets, const double *u_re_im) {
     if (!c) return fail(nullptr, RCS_ERR_ARG, "null context");
     const double *u[1] = {u_re_im};

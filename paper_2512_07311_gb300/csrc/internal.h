@@ -153,6 +153,11 @@ bool tc_pass_takes_substate(const Pass &p, int n);
 int launch_pass_tc_from_sub(void *psi, int n, const Pass &p, const void *d_ops, int *d_err, void *stream, bool tf32,
                             const void *sub, uint64_t tmask);
 
+// Test hook of the tensor-core kernels' bounded waits (process-wide): the wait limit and
+// the tile (of CTA 0) whose MMAs are skipped, as every launch reads them, and the setter.
+void tc_test_fault(long long *wait_cycles, int *skip_tile);
+void tc_set_test_fault(int skip_tile, long long wait_cycles);
+
 // Size in bytes of the operand image of one 6-qubit pass (BF16x3: 64 KB, TF32x3:
 // 96 KB), and its builder.
 size_t tc_ops_bytes(bool tf32);

@@ -97,6 +97,8 @@ struct PairArgs {
     int t1[pr::K];      // ascending targets of U1
     int t2[pr::K];      // ascending targets of U2
     uint64_t vmask;     // the 13 index bits of a tile
+    long long wait_cycles;  // limit of every wait (SM clock cycles)
+    int skip_tile;          // test hook: CTA 0 runs no GEMM 1 for its tile skip_tile (-1: none)
 };
 
 namespace {
@@ -234,6 +236,7 @@ __global__ void __launch_bounds__(pr::kThreads, 1) k_pair_tc(const __grid_consta
     const uint32_t bar_mw = bar0 + 96u, bar_mr = bar0 + 104u;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long lim = a.wait_cycles;
     const uint64_t V = a.vmask;
     // compact masks (tile bit positions) of the target and slice bits of each unitary
     uint32_t t1c = 0, t2c = 0;
@@ -335,8 +338,8 @@ __global__ void __launch_bounds__(pr::kThreads, 1) k_pair_tc(const __grid_consta
         if (my_tiles > 1) issue(1, 1);
         for (uint32_t i = 0; i < my_tiles; ++i) {
             const int b = i & 1;
-            if (!warp_wait<true>(bar_loaded(b), (i >> 1) & 1, abort_flag)) break;
-            if (i >= 2 && !warp_wait<true>(bar_done2(b), ((i - 2) >> 1) & 1, abort_flag)) break;
+            if (!warp_wait<true>(bar_loaded(b), (i >> 1) & 1, abort_flag, lim)) break;
+            if (i >= 2 && !warp_wait<true>(bar_done2(b), ((i - 2) >> 1) & 1, abort_flag, lim)) break;
             tc_fence_after();
             const float2 *stage = reinterpret_cast<const float2 *>(sm + kStage0 + b * kStageBytes);
             const uint32_t arow = acol_of(b) + (uint32_t(32 * q) << 16);
@@ -357,7 +360,7 @@ __global__ void __launch_bounds__(pr::kThreads, 1) k_pair_tc(const __grid_consta
             // this warp has read its part of stage b: once every loader warp has (bar_a1), the
             // stage takes tile i+2
             if (i + 2 < my_tiles) {
-                if (!warp_wait<true>(bar_a1(b), (i >> 1) & 1, abort_flag)) break;
+                if (!warp_wait<true>(bar_a1(b), (i >> 1) & 1, abort_flag, lim)) break;
                 issue(i + 2, b);
             }
         }
@@ -372,7 +375,7 @@ __global__ void __launch_bounds__(pr::kThreads, 1) k_pair_tc(const __grid_consta
         const int rowhalf = srow >> 6;                             // slice bit 6 of this row (warp-uniform)
         for (uint32_t i = 0; i < my_tiles; ++i) {
             const int b = i & 1;
-            if (!warp_wait<true>(bar_done1(b), (i >> 1) & 1, abort_flag)) break;
+            if (!warp_wait<true>(bar_done1(b), (i >> 1) & 1, abort_flag, lim)) break;
             tc_fence_after();
             const uint32_t drow = dcol_of(b) + (uint32_t(32 * q) << 16);
             const uint32_t arow = acol_of(b) + (uint32_t(32 * q) << 16);
@@ -409,7 +412,7 @@ __global__ void __launch_bounds__(pr::kThreads, 1) k_pair_tc(const __grid_consta
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(bar_mw);
-                if (!warp_wait<true>(bar_mw, uint32_t(h), abort_flag)) {
+                if (!warp_wait<true>(bar_mw, uint32_t(h), abort_flag, lim)) {
                     ok = false;
                     break;
                 }
@@ -440,7 +443,7 @@ __global__ void __launch_bounds__(pr::kThreads, 1) k_pair_tc(const __grid_consta
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(bar_mr);
-                if (!warp_wait<true>(bar_mr, uint32_t(h), abort_flag)) {
+                if (!warp_wait<true>(bar_mr, uint32_t(h), abort_flag, lim)) {
                     ok = false;
                     break;
                 }
@@ -467,7 +470,7 @@ __global__ void __launch_bounds__(pr::kThreads, 1) k_pair_tc(const __grid_consta
         };
         for (uint32_t i = 0; i < my_tiles; ++i) {
             const int b = i & 1;
-            if (!warp_wait<true>(bar_done2(b), (i >> 1) & 1, abort_flag)) break;
+            if (!warp_wait<true>(bar_done2(b), (i >> 1) & 1, abort_flag, lim)) break;
             tc_fence_after();
             float2 *const base = a.psi + (tile_base(i) | sb2);
             const uint32_t drow = dcol_of(b) + (uint32_t(32 * q) << 16);
@@ -510,7 +513,7 @@ __global__ void __launch_bounds__(pr::kThreads, 1) k_pair_tc(const __grid_consta
         // Two queues: GEMM 1 of tile n1 (needs its U1 operand and, two tiles back in the same
         // buffer, D stored) and GEMM 2 of tile n2 < n1 (needs its U2 operand). The issuer polls
         // both without blocking and issues whichever is ready, so neither waits behind the
-        // other's hand-off. It gives up after kTcWaitCycles without progress.
+        // other's hand-off. It gives up after the wait limit without progress.
         if (lane == 0) {
             const uint32_t img1 = smem_u32(sm), img2 = img1 + uint32_t(kOpBytes);
             uint32_t last_bar = 0, last_par = 0;
@@ -522,8 +525,11 @@ __global__ void __launch_bounds__(pr::kThreads, 1) k_pair_tc(const __grid_consta
                 if (n1 < my_tiles) {
                     const int b = n1 & 1;
                     const uint32_t par = (n1 >> 1) & 1;
-                    if (mbar_test_wait(bar_a1(b), par) &&
-                        (n1 < 2 || mbar_test_wait(bar_dfree(b), ((n1 - 2) >> 1) & 1))) {
+                    if (blockIdx.x == 0 && int(n1) == a.skip_tile) {
+                        // test hook: nothing issued or committed for this tile, so every wait on it
+                        // runs out
+                    } else if (mbar_test_wait(bar_a1(b), par) &&
+                               (n1 < 2 || mbar_test_wait(bar_dfree(b), ((n1 - 2) >> 1) & 1))) {
                         tc_fence_after();
                         gemm_cx(img1, dcol_of(b), acol_of(b));
                         mma_commit(bar_done1(b));
@@ -552,7 +558,7 @@ __global__ void __launch_bounds__(pr::kThreads, 1) k_pair_tc(const __grid_consta
                     t0 = clock64();
                 } else {
                     if (*abort_flag) break;
-                    if (clock64() - t0 > kTcWaitCycles) {
+                    if (clock64() - t0 > lim) {
                         *abort_flag = 1;
                         break;
                     }
@@ -561,7 +567,7 @@ __global__ void __launch_bounds__(pr::kThreads, 1) k_pair_tc(const __grid_consta
             if (*abort_flag && committed) {
                 // drain: the last committed MMAs must finish before tensor memory is freed
                 const long long t1 = clock64();
-                while (!mbar_try_wait(last_bar, last_par) && clock64() - t1 < kTcWaitCycles) {
+                while (!mbar_try_wait(last_bar, last_par) && clock64() - t1 < lim) {
                 }
             }
         }
@@ -653,6 +659,7 @@ int launch_pair_tc(void *psi, int n, const Pass &p1, const Pass &p2, const void 
     uint64_t V = T;
     for (int b = 0; b < n && std::popcount(V) < kBits; ++b) V |= 1ull << b;
     a.vmask = V;
+    tc_test_fault(&a.wait_cycles, &a.skip_tile);
     const unsigned grid = unsigned(std::min<uint64_t>(a.tiles, uint64_t(device_sm_count())));
     k_pair_tc<<<grid, kThreads, kAlloc, static_cast<cudaStream_t>(stream)>>>(a);
     return launch_status("tensor-core pair pass");

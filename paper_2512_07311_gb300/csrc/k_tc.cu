@@ -42,6 +42,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 
 #include "dev_common.cuh"
@@ -84,7 +85,6 @@ struct Layout {
     static_assert(kAlloc <= 227 * 1024, "shared memory");
 };
 constexpr uint32_t kTmemCols = 512;
-constexpr long long kWaitCycles = kTcWaitCycles;
 // instruction descriptor: D f32, A bf16, B bf16, both K-major, N = 128, M = 128
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(NR >> 3) << 17) | (uint32_t(M >> 4) << 24);
 // TF32 variant: D f32, A tf32, B tf32, both K-major, N = 128 (Re outputs, then Im), M = 128
@@ -104,6 +104,8 @@ struct TcArgs {
     // index bits in tmask, in order). The pass writes the whole state to psi.
     const float2 *sub;
     uint64_t tmask;
+    long long wait_cycles;  // limit of every wait (SM clock cycles)
+    int skip_tile;          // test hook: CTA 0 issues no MMAs for its tile skip_tile (-1: none)
 };
 
 // Position of compact tile index c in the memory-order stage: XOR-swizzles bits
@@ -175,6 +177,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
     volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + L::kMisc + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long lim = a.wait_cycles;
     int t[K];
 #pragma unroll
     for (int i = 0; i < K; ++i) t[i] = a.t[i];
@@ -277,11 +280,11 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
         if constexpr (kTf32) {
             if (i < 1) return true;
             const uint32_t j = i - 1;
-            return warp_wait<!kTf32>(h ? bar_done(int(j & 1)) : bar_done_a(int(j & 1)), (j >> 1) & 1, abort_flag);
+            return warp_wait<!kTf32>(h ? bar_done(int(j & 1)) : bar_done_a(int(j & 1)), (j >> 1) & 1, abort_flag, lim);
         } else {
             if (i < 2) return true;
             const uint32_t j = i - 2;
-            return warp_wait<!kTf32>(bar_done(int(j & 1)), (j >> 1) & 1, abort_flag);
+            return warp_wait<!kTf32>(bar_done(int(j & 1)), (j >> 1) & 1, abort_flag, lim);
         }
     };
     // TMEM column of the A region for K half h (TF32) or the A_hi image (BF16).
@@ -470,7 +473,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
         if (my_tiles > 1) issue(1, 1);
         for (uint32_t i = 0; i < my_tiles; ++i) {
             const int b = i & 1;
-            if (!warp_wait<!kTf32>(bar_loaded(b), (i >> 1) & 1, abort_flag)) break;
+            if (!warp_wait<!kTf32>(bar_loaded(b), (i >> 1) & 1, abort_flag, lim)) break;
             if (!wait_a_free(i, h)) break;
             tc_fence_after();
             const float2 *stage = reinterpret_cast<const float2 *>(sm + L::kStage0 + b * kStageBytes);
@@ -491,7 +494,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
             // it (tiles 0 and 1 were issued up front); converting tile i first keeps its
             // MMA and epilogue running while tile i+1 is in flight
             if (i >= 1 && i + 1 < my_tiles) {
-                if (!warp_wait<!kTf32>(bar_sfree(b ^ 1), ((i - 1) >> 1) & 1, abort_flag)) break;
+                if (!warp_wait<!kTf32>(bar_sfree(b ^ 1), ((i - 1) >> 1) & 1, abort_flag, lim)) break;
                 issue(i + 1, b ^ 1);
             }
         }
@@ -514,7 +517,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
         };
         for (uint32_t i = 0; i < my_tiles; ++i) {
             const int b = i & 1;
-            if (!warp_wait<!kTf32>(bar_done(b), (i >> 1) & 1, abort_flag)) break;
+            if (!warp_wait<!kTf32>(bar_done(b), (i >> 1) & 1, abort_flag, lim)) break;
             tc_fence_after();
             const uint64_t tile = uint64_t(blockIdx.x) + uint64_t(i) * gridDim.x;
             const uint64_t base = slice_base(tile * M + srow, t);
@@ -555,7 +558,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
         const uint32_t csr = cs[srow];
         for (uint32_t i = 0; i < my_tiles; ++i) {
             const int b = i & 1;
-            if (!warp_wait<!kTf32>(bar_done(b), (i >> 1) & 1, abort_flag)) break;
+            if (!warp_wait<!kTf32>(bar_done(b), (i >> 1) & 1, abort_flag, lim)) break;
             tc_fence_after();
             float2 *stage = reinterpret_cast<float2 *>(sm + L::kStage0 + b * kStageBytes);
             const uint32_t dbase = dcol_of(b) + (uint32_t(32 * q) << 16);
@@ -572,7 +575,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
                 mbar_arrive(bar_free(b));
                 mbar_arrive(bar_outready(b));
             }
-            if (!warp_wait<!kTf32>(bar_outready(b), (i >> 1) & 1, abort_flag)) break;
+            if (!warp_wait<!kTf32>(bar_outready(b), (i >> 1) & 1, abort_flag, lim)) break;
             const uint64_t tile = uint64_t(blockIdx.x) + uint64_t(i) * gridDim.x;
             const uint64_t tbase = slice_base(tile * M, t);
 #pragma unroll 8
@@ -598,8 +601,10 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
             for (uint32_t i = 0; i < my_tiles; ++i) {
                 const int b = i & 1;
                 const uint32_t par = (i >> 1) & 1;
-                if (!mbar_wait<!kTf32>(bar_full(b), par, abort_flag)) break;
-                if (i >= 2 && !mbar_wait<!kTf32>(bar_free(b), ((i >> 1) - 1) & 1, abort_flag)) break;
+                if (!mbar_wait<!kTf32>(bar_full(b), par, abort_flag, lim)) break;
+                if (i >= 2 && !mbar_wait<!kTf32>(bar_free(b), ((i >> 1) - 1) & 1, abort_flag, lim)) break;
+                // test hook: nothing issued or committed for this tile, so every wait on it runs out
+                if (blockIdx.x == 0 && int(i) == a.skip_tile) continue;
                 tc_fence_after();
                 const uint32_t dcol = dcol_of(b), acol = acol_of(b);
                 if constexpr (kTf32) {
@@ -627,7 +632,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
                     };
                     half(0);
                     commit(bar_done_a(b), par);
-                    if (!mbar_wait<!kTf32>(bar_full1(b), par, abort_flag)) break;
+                    if (!mbar_wait<!kTf32>(bar_full1(b), par, abort_flag, lim)) break;
                     tc_fence_after();
                     half(1);
                 } else {
@@ -648,7 +653,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
             if (*abort_flag && committed) {
                 // drain: the last committed MMAs must finish before tensor memory is freed
                 const long long t0 = clock64();
-                while (!mbar_try_wait(last_bar, last_par) && clock64() - t0 < kWaitCycles) {
+                while (!mbar_try_wait(last_bar, last_par) && clock64() - t0 < lim) {
                 }
             }
         }
@@ -665,6 +670,21 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_fused_tc(const __grid_const
 }
 
 // ---------------------------------------------------------------- host side
+
+namespace {
+std::atomic<long long> g_tc_wait_cycles{kTcWaitCycles};
+std::atomic<int> g_tc_skip_tile{-1};
+}  // namespace
+
+void tc_test_fault(long long *wait_cycles, int *skip_tile) {
+    *wait_cycles = g_tc_wait_cycles.load();
+    *skip_tile = g_tc_skip_tile.load();
+}
+
+void tc_set_test_fault(int skip_tile, long long wait_cycles) {
+    g_tc_skip_tile.store(skip_tile < 0 ? -1 : skip_tile);
+    g_tc_wait_cycles.store(wait_cycles > 0 ? wait_cycles : kTcWaitCycles);
+}
 
 static uint16_t bf16_rn_bits(float f) {
     uint32_t u;
@@ -790,6 +810,7 @@ static int launch_tc(void *psi, int n, const Pass &p, const void *d_ops, int *d_
     a.tmask = tmask;
     a.ops = static_cast<const uint4 *>(d_ops);
     a.err = d_err;
+    tc_test_fault(&a.wait_cycles, &a.skip_tile);
     a.tiles = uint32_t((1ull << (n - K)) / M);
     for (int i = 0; i < K; ++i) a.t[i] = p.t[i];
     // qubits varying inside a tile: the targets plus the 7 lowest other qubits

@@ -1,6 +1,7 @@
 // PTX wrappers for the tensor-core kernels: mbarriers, tcgen05 tensor-memory loads and
 // stores, shared-memory matrix descriptors, MMA commits, and the hi/lo operand splits.
-// Every wait is bounded (kTcWaitCycles of SM clock, about one second at 2 GHz).
+// Every wait is bounded: by the limit the kernel is given (kTcWaitCycles of SM clock,
+// about one second at 2 GHz, unless a test shortens it).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -63,11 +64,11 @@ __device__ __forceinline__ bool mbar_try_wait_suspend(uint32_t bar, uint32_t par
 // kSuspend: park the waiting thread in the hardware (the BF16 variants measured about 1%
 // faster per pass with it; the TF32 variants, whose K-half hand-offs are shorter, slower).
 template <bool kSuspend>
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, long long limit) {
     const long long t0 = clock64();
     while (!(kSuspend ? mbar_try_wait_suspend(bar, parity) : mbar_try_wait(bar, parity))) {
         if (*abort_flag) return false;
-        if (clock64() - t0 > kTcWaitCycles) {
+        if (clock64() - t0 > limit) {
             *abort_flag = 1;
             return false;
         }
@@ -80,9 +81,9 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
 // acquiring test so the whole warp is ordered after the phase. The phase cannot
 // move on before this warp arrives on its own barrier, so the test cannot miss it.
 template <bool kSuspend>
-__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, long long limit) {
     int ok = 1;
-    if ((threadIdx.x & 31) == 0) ok = mbar_wait<kSuspend>(bar, parity, abort_flag) ? 1 : 0;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait<kSuspend>(bar, parity, abort_flag, limit) ? 1 : 0;
     ok = __shfl_sync(0xffffffffu, ok, 0);
     if (ok) (void)mbar_try_wait(bar, parity);
     __syncwarp();
