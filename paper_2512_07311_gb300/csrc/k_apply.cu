@@ -150,9 +150,24 @@ struct SimtArgs {
     uint64_t slices;
 };
 
+// Resident CTAs per SM for width K, set by the registers the mat-vec needs without
+// spilling (the two stages of 256 slices x 2^K amplitudes fit in shared memory).
 template <int K>
-__global__ void __launch_bounds__(256, (K >= 5 ? 1 : 2)) k_fused_simt(float2 *__restrict__ psi, const SimtArgs<K> a) {
+constexpr int simt_blocks_per_sm() {
+    return K >= 5 ? 1 : (K == 4 ? 2 : 3);
+}
+
+// One thread per 2^K-amplitude slice, persistent over the slices (grid-stride). Each
+// thread double-buffers its own slice through shared memory with cp.async: the copies of
+// its next slice are in flight while it multiplies the current one, so the loads of a
+// slice never wait behind the previous slice's mat-vec and stores. The stage slots are
+// private to the thread (slot [b][j][thread]), so no block barrier is needed; lanes of a
+// warp take neighbouring slices, and with no target below qubit 5 every copy and store
+// instruction of a warp covers 256 contiguous bytes.
+template <int K>
+__global__ void __launch_bounds__(256, simt_blocks_per_sm<K>()) k_fused_simt(float2 *__restrict__ psi, const SimtArgs<K> a) {
     constexpr int D = 1 << K;
+    extern __shared__ float2 stage[];  // [2][D][256]
     // target offsets of local index j, warp-uniform; read back through a volatile
     // pointer at every use so they are not held in registers across the mat-vec
     __shared__ uint64_t offs_s[D];
@@ -166,15 +181,35 @@ __global__ void __launch_bounds__(256, (K >= 5 ? 1 : 2)) k_fused_simt(float2 *__
     __syncthreads();
     const volatile uint64_t *offs = offs_s;
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-#pragma unroll 1
-    for (uint64_t s = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < a.slices; s += stride) {
-        uint64_t base = s;
+    const uint32_t slot0 = uint32_t(__cvta_generic_to_shared(stage)) + threadIdx.x * 8u;
+    auto base_of = [&](uint64_t sl) {
+        uint64_t b = sl;
 #pragma unroll
-        for (int i = 0; i < K; ++i) base = insert_zero(base, a.t[i]);
-        float2 *p = psi + base;
+        for (int i = 0; i < K; ++i) b = insert_zero(b, a.t[i]);
+        return b;
+    };
+    auto issue = [&](uint64_t sl, int buf) {
+        if (sl < a.slices) {
+            const float2 *p = psi + base_of(sl);
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                const uint32_t dst = slot0 + uint32_t((buf * D + j) * 256) * 8u;
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(p + offs[j]) : "memory");
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    uint64_t s = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    issue(s, 0);
+    int buf = 0;
+#pragma unroll 1
+    for (; s < a.slices; s += stride, buf ^= 1) {
+        issue(s + stride, buf ^ 1);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");  // this slice's copies have landed
         float2 v[D];
 #pragma unroll
-        for (int j = 0; j < D; ++j) v[j] = p[offs[j]];
+        for (int j = 0; j < D; ++j) v[j] = stage[(buf * D + j) * 256 + threadIdx.x];
+        float2 *p = psi + base_of(s);
 #pragma unroll
         for (int j = 0; j < D; ++j) {
             float2 acc = make_float2(0.f, 0.f);
@@ -189,6 +224,7 @@ __global__ void __launch_bounds__(256, (K >= 5 ? 1 : 2)) k_fused_simt(float2 *__
             p[offs[j]] = acc;
         }
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 __global__ void k_init_zero(float4 *__restrict__ psi4, uint64_t n4) {
@@ -294,7 +330,18 @@ static int launch_simt_k(float2 *psi, int n, const Pass &p, cudaStream_t st) {
     for (int i = 0; i < K; ++i) a.t[i] = p.t[i];
     a.slices = 1ull << (n - K);
     const int threads = 256;
-    k_fused_simt<K><<<grid_for(a.slices, threads, device_sm_count(), 8), threads, 0, st>>>(psi, a);
+    const int smem = 2 * (1 << K) * threads * int(sizeof(float2));
+    static bool attr_done[5][64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !attr_done[K - 1][dev]) {
+        const cudaError_t e = cudaFuncSetAttribute(k_fused_simt<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return note_launch_error("fused kernel shared-memory attribute", e);
+        if (dev >= 0 && dev < 64) attr_done[K - 1][dev] = true;
+    }
+    // persistent: the resident CTAs, never more than the slices need
+    const unsigned grid = grid_for(a.slices, threads, device_sm_count(), simt_blocks_per_sm<K>());
+    k_fused_simt<K><<<grid, threads, smem, st>>>(psi, a);
     return check_launch();
 }
 
