@@ -284,12 +284,12 @@ def run_reference(args, rank: int, world: int):
 
 # ------------------------------------------------------------------ our arm
 
-def run_batch(args, torch, capi):
-    """64 seeded circuits (16-26 qubits, 10-20 cycles, 10^5 shots each) in one graph launch.
-    The tensor-core engine (one launch chain per circuit: fused 6-qubit passes with each
-    circuit's own layout and sub-state prefix, then sampling and XEB) is the line's value;
-    the persistent FP32 engine (every pass of every circuit as items of one cooperative
-    launch, fusion width autotuned) is timed beside it in `compare`."""
+def batch64_measure(args, torch, capi, precision: str):
+    """64 seeded circuits (16-26 qubits, 10-20 cycles, 10^5 shots each) in one graph launch,
+    through the tensor-core engine (every pass of every circuit in one persistent tensor-core
+    launch, tiles per work item autotuned; then sampling and XEB) and the persistent FP32 engine (every
+    pass of every circuit as items of one cooperative launch, fusion width and item size
+    autotuned). Returns both timings with their byte counts."""
     circs = C.batch_workload(64, 1000)
     shots = args.shots or 100_000
     stream = torch.cuda.current_stream()
@@ -328,16 +328,29 @@ def run_batch(args, torch, capi):
             total += pi["zero_hbm_bytes"]
         return total
 
-    prec = capi.PRECISIONS[args.precision]
+    prec = capi.PRECISIONS[precision]
     ms, infos, xebs = timed(prec)
     apply_bytes = state_bytes(prec, infos)
     sample_bytes = sum(16.0 * 2**c.n_qubits for c in circs)  # block sums + the sampled blocks, about two reads
     ms_f, infos_f, xebs_f = timed(capi.RCS_PREC_FP32_FUSED)
     bytes_f = state_bytes(capi.RCS_PREC_FP32_FUSED, infos_f)
+    return {"circs": circs, "shots": shots, "ms": ms, "infos": infos, "xebs": xebs, "apply_bytes": apply_bytes,
+            "sample_bytes": sample_bytes, "ms_f": ms_f, "infos_f": infos_f, "xebs_f": xebs_f, "bytes_f": bytes_f,
+            "peak": peaks["hbm_gbs"]}
+
+
+def run_batch(args, torch, capi):
+    """The 64-circuit batched workload as its own JSON line: the tensor-core engine is the
+    line's value, the persistent FP32 engine is in `compare`."""
+    m = batch64_measure(args, torch, capi, args.precision)
+    circs, shots, ms, infos, xebs = m["circs"], m["shots"], m["ms"], m["infos"], m["xebs"]
+    apply_bytes, sample_bytes, ms_f, infos_f, xebs_f, bytes_f = (m["apply_bytes"], m["sample_bytes"], m["ms_f"],
+                                                                 m["infos_f"], m["xebs_f"], m["bytes_f"])
+    peaks = {"hbm_gbs": m["peak"]}
     line = {"metric": "64-circuit batched workload time (s)", "value": ms / 1e3, "unit": "s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": False, "data": "synthetic", "dtype": f"{args.precision} (fp32 accumulate); fp32 state",
-            "config": {"workload": "batch64", "circuits": len(circs), "engine": "tensor-core launch chains",
+            "config": {"workload": "batch64", "circuits": len(circs), "engine": "persistent tensor-core kernel",
                        "qubits": [c.n_qubits for c in circs], "shots_per_circuit": shots,
                        "k": [inf["k"] for inf in infos], "passes": [inf["n_passes"] for inf in infos],
                        "l2": "states of 16-26 qubits: the largest (512 MiB) exceed L2; no flush between steps"},
@@ -560,6 +573,15 @@ def main():
     capi.rcs_plan_destroy(plan)
     capi.rcs_destroy(ctx)
     clocks = clk.summary()
+    if not args.no_compare and world == 1 and args.precision == "bf16x3":
+        # the batched workload (64 circuits of 16-26 qubits), timed in the same run
+        m = batch64_measure(args, torch, capi, "bf16x3")
+        both = m["apply_bytes"] + m["sample_bytes"]
+        compare["batch64"] = {
+            "tensor_core_s": m["ms"] / 1e3, "fp32_persistent_s": m["ms_f"] / 1e3,
+            "tensor_core_frac_of_hbm": both / (m["ms"] / 1e3) / 1e9 / m["peak"],
+            "fp32_frac_of_hbm": (m["bytes_f"] + m["sample_bytes"]) / (m["ms_f"] / 1e3) / 1e9 / m["peak"],
+            "xeb_mean_tensor_core": float(np.mean(m["xebs"])), "steps": args.steps}
     if rank == 0:
         line = {
             "metric": METRIC, "value": per_circuit_seconds(ms_step, world), "unit": "s", "n_gpus": world,

@@ -3,7 +3,7 @@
 // width of every circuit chosen by timed trials.
 //
 // Work items. Each circuit i is planned (FP32 fused, k <= 5) into passes; each pass
-// is cut into items of kSlicesPerItem slices. The host lays the items out in rounds
+// is cut into items of a few thousand slices. The host lays the items out in rounds
 // -- round r holds pass r of every circuit that has one -- so every item of pass p
 // of circuit i is handed out before any item of its pass p+1. A CTA takes the next
 // item from a global counter, waits until circuit i has finished all items of its
@@ -47,13 +47,17 @@ using namespace rcs;
 namespace {
 
 constexpr int kThreads = 256;
-constexpr uint32_t kSlicesPerItem = 2048;  // 8 slices per thread
+constexpr uint32_t kSlicesPerItem = 2048;  // default item: 8 slices per thread
+// item sizes the autotuner tries (slices; a multiple of the CTA's threads)
+constexpr uint32_t kItemSizes[] = {1024, 2048, 4096, 8192};
 constexpr int kMaxK = 5;
 
 struct BInst {
     float2 *psi;
     uint32_t n;
     uint32_t items_per_pass;
+    uint32_t slices_per_item;
+    uint32_t reserved;
 };
 struct BPass {
     int32_t k;
@@ -172,8 +176,8 @@ __global__ void __launch_bounds__(kThreads) k_batch_apply(const __grid_constant_
         __syncthreads();
         const uint64_t item_in_pass = s_item - sg.first_item;
         const uint64_t nslices = 1ull << (in.n - ps.k);
-        const uint64_t s0 = item_in_pass * kSlicesPerItem;
-        const uint64_t s1 = s0 + kSlicesPerItem < nslices ? s0 + kSlicesPerItem : nslices;
+        const uint64_t s0 = item_in_pass * in.slices_per_item;
+        const uint64_t s1 = s0 + in.slices_per_item < nslices ? s0 + in.slices_per_item : nslices;
         int t[kMaxK];
 #pragma unroll
         for (int i = 0; i < kMaxK; ++i) t[i] = ps.t[i];
@@ -211,23 +215,31 @@ struct InstHost {
     void *d_sub = nullptr;
     int prefix = 0;
     std::vector<SubStage> stages;
+    bool persistent = false;  // tensor-core engine: its passes run in the persistent kernel
     float2 *psi = nullptr;
     uint64_t *bsum = nullptr, *bpre = nullptr, *chunk = nullptr, *total = nullptr;
     uint64_t *d_bits = nullptr;  // shots
     uint64_t *d_order = nullptr;  // shots: the sampler's scratch
     double *d_xeb = nullptr;     // result + partials
     uint64_t items_per_pass = 0;
+    uint32_t slices_per_item = kSlicesPerItem;  // FP32 engine: the work-item size
 };
 
 // ---- autotuner: chosen fusion width per qubit count, by timed trials (cached per device)
 std::mutex g_tune_mu;
-std::map<std::pair<int, int>, int> g_tuned;  // (device, n) -> k
+struct Tuned {
+    int k;
+    uint32_t slices_per_item;
+};
+std::map<std::pair<int, int>, Tuned> g_tuned;  // (device, n) -> fusion width and item size
 
 }  // namespace
 
 struct rcs_batch {
     int dev = 0;
-    bool tc = false;  // tensor-core engine (one launch chain per circuit)
+    bool tc = false;  // tensor-core engine
+    BtcPlan *btc = nullptr;        // tensor-core engine: the persistent kernel's tables
+    uint32_t tiles_per_item = 0;   // ... and their chosen item size
     std::vector<InstHost> inst;
     BInst *d_inst = nullptr;
     BPass *d_pass = nullptr;
@@ -300,9 +312,9 @@ void build_tables(const std::vector<InstHost> &inst, std::vector<BPass> *passes,
     *nitems = item;
 }
 
-uint64_t items_per_pass(int n, int k) {
+uint64_t items_per_pass(int n, int k, uint32_t slices_per_item) {
     const uint64_t slices = 1ull << (n - k);
-    return (slices + kSlicesPerItem - 1) / kSlicesPerItem;
+    return (slices + slices_per_item - 1) / slices_per_item;
 }
 
 int launch_apply(rcs_batch *b, cudaStream_t st, uint64_t nitems) {
@@ -341,7 +353,7 @@ int persistent_grid() {
 
 // Times `reps` passes of width k on an n-qubit scratch state through the persistent
 // kernel (the same code path the batch runs) and returns ms per pass.
-double time_trial(int n, int k, float2 *scratch, rcs_batch *tmpl) {
+double time_trial(int n, int k, uint32_t spi, float2 *scratch, rcs_batch *tmpl) {
     InstHost h;
     h.n = n;
     h.psi = scratch;
@@ -358,7 +370,7 @@ double time_trial(int n, int k, float2 *scratch, rcs_batch *tmpl) {
         for (int j = 0; j < d; ++j) p.U[size_t(j) * d + ((j + 1) % d)] = cd(0.0, 1.0);  // a permutation: unitary
         h.plan.passes.push_back(p);
     }
-    h.items_per_pass = items_per_pass(n, k);
+    h.items_per_pass = items_per_pass(n, k, spi);
     rcs_batch t;
     t.dev = tmpl->dev;
     t.grid = tmpl->grid;
@@ -370,7 +382,7 @@ double time_trial(int n, int k, float2 *scratch, rcs_batch *tmpl) {
     std::vector<BSeg> segs;
     std::vector<uint32_t> pass0;
     build_tables(one, &passes, &U, &segs, &pass0, &t.nitems);
-    BInst bi{scratch, uint32_t(n), uint32_t(h.items_per_pass)};
+    BInst bi{scratch, uint32_t(n), uint32_t(h.items_per_pass), spi, 0};
     double ms = -1.0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaMalloc(&t.d_inst, sizeof(BInst)) == cudaSuccess && cudaMalloc(&t.d_pass, passes.size() * sizeof(BPass)) == cudaSuccess &&
@@ -416,30 +428,35 @@ double time_trial(int n, int k, float2 *scratch, rcs_batch *tmpl) {
     return ms;
 }
 
-// Chooses k in [2, 5] minimising (passes of the circuit at width k) x (measured ms per
-// pass of width k at this qubit count); cached per (device, n).
-int autotune_k(rcs_batch *b, int n, const std::vector<HostGate> &hg, float2 *scratch) {
+// Chooses the fusion width k in [2, 5] and the work-item size (slices per item, the
+// tile each CTA takes from the queue) minimising (passes of the circuit at width k) x
+// (measured ms per pass of width k in items of that size at this qubit count); cached
+// per (device, n).
+Tuned autotune(rcs_batch *b, int n, const std::vector<HostGate> &hg, float2 *scratch) {
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tuned.find({b->dev, n});
         if (it != g_tuned.end()) return it->second;
     }
-    int best_k = std::min(4, n);
-    double best = 1e300;
+    Tuned best{std::min(4, n), kSlicesPerItem};
+    double best_ms = 1e300;
     for (int k = 2; k <= std::min(kMaxK, n); ++k) {
         std::vector<Pass> passes;
         plan_fuse(n, hg, k, 0, &passes);
-        const double ms = time_trial(n, k, scratch, b);
-        if (ms <= 0) continue;
-        const double est = ms * double(passes.size());
-        if (est < best) {
-            best = est;
-            best_k = k;
+        for (uint32_t spi : kItemSizes) {
+            if (spi > 2 * kSlicesPerItem && (1ull << (n - k)) < uint64_t(spi) * 64) continue;  // too few items
+            const double ms = time_trial(n, k, spi, scratch, b);
+            if (ms <= 0) continue;
+            const double est = ms * double(passes.size());
+            if (est < best_ms) {
+                best_ms = est;
+                best = Tuned{k, spi};
+            }
         }
     }
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tuned[{b->dev, n}] = best_k;
-    return best_k;
+    g_tuned[{b->dev, n}] = best;
+    return best;
 }
 
 void free_batch(rcs_batch *b) {
@@ -468,6 +485,7 @@ void free_batch(rcs_batch *b) {
     cudaFree(b->d_next);
     cudaFree(b->d_done);
     cudaFree(b->d_err);
+    btc_destroy(b->btc);
     delete b;
 }
 
@@ -504,19 +522,138 @@ int record_chain(rcs_batch *b, InstHost &h, cudaStream_t st) {
     return launch_sampling(b, h, st);
 }
 
+// The circuit's passes as steps of the persistent tensor-core kernel: the stages' passes on
+// their sub-states, then the full-state passes; the first pass of each stage and the first
+// full pass read the state before them as a sub-state (the very first reads |0...0>), so no
+// zero fill or expansion is left. False if a pass cannot run there (not a 6-qubit
+// tensor-core pass, a state under 13 qubits) or no full pass follows the last stage.
+bool persistent_steps(const InstHost &h, std::vector<BtcStep> *out) {
+    out->clear();
+    const Plan &plan = h.plan;
+    if (h.n < kTcK + 7 || plan.passes.empty() || plan.tc_offset.size() != plan.passes.size() || !h.d_ops) return false;
+    for (size_t i = 0; i < plan.passes.size(); ++i)
+        if (plan.passes[i].kind != PASS_TC || plan.passes[i].k != kTcK || plan.tc_offset[i] < 0) return false;
+    const void *cur = nullptr;  // input of the next stage's first pass (null: |0...0>)
+    uint64_t cur_mask = 0;      // its qubits, in the circuit's stored numbering
+    size_t first = 0;
+    auto step = [&](void *dst, int m, size_t i, const Pass &p, bool stage_first, uint64_t tmask) {
+        BtcStep s;
+        s.dst = dst;
+        s.m = m;
+        s.ops = h.d_ops + plan.tc_offset[i];
+        s.p = p;
+        if (stage_first) {
+            s.from_zero = cur == nullptr;
+            s.src = cur;
+            s.src_m = std::popcount(cur_mask);
+            s.tmask = tmask;
+        }
+        out->push_back(s);
+    };
+    if (h.prefix > 0) {
+        uint8_t *buf = static_cast<uint8_t *>(h.d_sub);
+        for (const SubStage &st : h.stages) {
+            const int m = std::popcount(st.tmask);
+            void *next = buf;
+            buf += size_t(8) << m;
+            if (st.count == 0) continue;
+            if (m < kTcK + 7) return false;
+            uint64_t inner = 0;  // the previous sub-state's qubits, numbered inside this one
+            for (int q = 0, k = 0; q < plan.n; ++q)
+                if ((st.tmask >> q) & 1) {
+                    if ((cur_mask >> q) & 1) inner |= 1ull << k;
+                    ++k;
+                }
+            for (int i = st.first; i < st.first + st.count; ++i)
+                step(next, m, size_t(i), substate_pass(plan.passes[size_t(i)], st.tmask), i == st.first, inner);
+            cur = next;
+            cur_mask = st.tmask;
+        }
+        first = size_t(h.stages.back().first + h.stages.back().count);
+        if (first >= plan.passes.size()) return false;
+    }
+    for (size_t i = first; i < plan.passes.size(); ++i) step(h.psi, h.n, i, plan.passes[i], i == first, cur_mask);
+    return true;
+}
+
+// Tensor-core engine: the circuits the persistent kernel cannot run go first, one launch
+// chain each (with their sampling); then the persistent kernel applies every pass of all
+// the others in one launch, and their samplers and XEB run on parallel branches.
 int record_tc(rcs_batch *b) {
     cudaStream_t s0 = b->cap;
-    BCUDA(b, cudaEventRecord(b->ev[0], s0), "fork event");
-    for (size_t j = 0; j < b->side.size(); ++j) BCUDA(b, cudaStreamWaitEvent(b->side[j], b->ev[0], 0), "fork");
-    // largest circuits first, so that the small ones fill in behind them
-    std::vector<size_t> order(b->inst.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return b->inst[x].n > b->inst[y].n; });
-    for (size_t r = 0; r < order.size(); ++r)
-        if (int rc = record_chain(b, b->inst[order[r]], b->side[r % b->side.size()]); rc != RCS_OK) return rc;
-    for (size_t j = 0; j < b->side.size(); ++j) {
-        BCUDA(b, cudaEventRecord(b->ev[1 + j], b->side[j]), "join event");
-        BCUDA(b, cudaStreamWaitEvent(s0, b->ev[1 + j], 0), "join");
+    std::vector<size_t> chains, rest;
+    for (size_t i = 0; i < b->inst.size(); ++i) (b->inst[i].persistent ? rest : chains).push_back(i);
+    auto fork = [&]() -> int {
+        BCUDA(b, cudaEventRecord(b->ev[0], s0), "fork event");
+        for (size_t j = 0; j < b->side.size(); ++j) BCUDA(b, cudaStreamWaitEvent(b->side[j], b->ev[0], 0), "fork");
+        return RCS_OK;
+    };
+    auto join = [&]() -> int {
+        for (size_t j = 0; j < b->side.size(); ++j) {
+            BCUDA(b, cudaEventRecord(b->ev[1 + j], b->side[j]), "join event");
+            BCUDA(b, cudaStreamWaitEvent(s0, b->ev[1 + j], 0), "join");
+        }
+        return RCS_OK;
+    };
+    int rc = RCS_OK;
+    if (!chains.empty()) {
+        if ((rc = fork()) != RCS_OK) return rc;
+        for (size_t r = 0; r < chains.size(); ++r)
+            if ((rc = record_chain(b, b->inst[chains[r]], b->side[r % b->side.size()])) != RCS_OK) return rc;
+        if ((rc = join()) != RCS_OK) return rc;
+    }
+    if (rest.empty()) return RCS_OK;
+    if ((rc = btc_launch(b->btc, b->d_err, b->wait_cycles, b->skip_item, s0)) != RCS_OK)
+        return bfail(b, rc, "persistent tensor-core launch: " + take_launch_error());
+    if ((rc = fork()) != RCS_OK) return rc;
+    for (size_t r = 0; r < rest.size(); ++r)
+        if ((rc = launch_sampling(b, b->inst[rest[r]], b->side[r % b->side.size()])) != RCS_OK) return rc;
+    return join();
+}
+
+// Tiles per work item of the persistent tensor-core kernel: each candidate builds its
+// tables and times three launches (after one untimed) on the batch's own states; the
+// fastest is kept. Every candidate must finish without a device error.
+constexpr uint32_t kTilesPerItem[] = {2, 4, 8, 16, 32};
+
+int tune_persistent(rcs_batch *b, const std::vector<std::vector<BtcStep>> &steps) {
+    const bool tf32 = b->inst.front().plan.precision == RCS_PREC_TF32X3;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    BCUDA(b, cudaEventCreate(&e0), "event");
+    BCUDA(b, cudaEventCreate(&e1), "event");
+    float best_ms = 0.f;
+    int rc = RCS_OK;
+    for (uint32_t g : kTilesPerItem) {
+        BtcPlan *pl = nullptr;
+        if ((rc = btc_create(steps, tf32, g, &pl)) != RCS_OK) break;
+        float ms = 0.f;
+        rc = btc_launch(pl, b->d_err, b->wait_cycles, -1, b->cap);
+        if (rc == RCS_OK && cudaEventRecord(e0, b->cap) != cudaSuccess) rc = RCS_ERR_CUDA;
+        for (int r = 0; r < 3 && rc == RCS_OK; ++r) rc = btc_launch(pl, b->d_err, b->wait_cycles, -1, b->cap);
+        if (rc == RCS_OK && (cudaEventRecord(e1, b->cap) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            rc = RCS_ERR_CUDA;
+        int h[2] = {0, 0};
+        if (rc == RCS_OK && cudaMemcpy(h, b->d_err, 8, cudaMemcpyDeviceToHost) != cudaSuccess) rc = RCS_ERR_CUDA;
+        if (rc == RCS_OK && h[0] != 0) rc = (h[0] & kErrTimeout) ? RCS_ERR_TIMEOUT : RCS_ERR_CUDA;
+        if (rc != RCS_OK) {
+            btc_destroy(pl);
+            break;
+        }
+        if (!b->btc || ms < best_ms) {
+            btc_destroy(b->btc);
+            b->btc = pl;
+            b->tiles_per_item = g;
+            best_ms = ms;
+        } else {
+            btc_destroy(pl);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != RCS_OK) {
+        cudaMemset(b->d_err, 0, 8);
+        return bfail(b, rc, "persistent tensor-core trial: " + take_launch_error());
     }
     return RCS_OK;
 }
@@ -656,12 +793,27 @@ int rcs_batch_create(const rcs_batch_item *items, size_t n_items, const rcs_opts
                 h.prefix = plan_stages(h.plan, &h.stages);
                 if (h.prefix > 0) BCUDA(b, cudaMalloc(&h.d_sub, substage_bytes(h.stages)), "sub-state");
             }
-            if (int rc = tc_prepare_device(); rc != RCS_OK) {
+            int prc = tc_prepare_device();
+            if (prc == RCS_OK) prc = simt_prepare_device();
+            if (prc != RCS_OK) {
                 std::string m = take_launch_error();
                 free_batch(b);
-                return set_thread_error(rc, m);
+                return set_thread_error(prc, m);
             }
             BCUDA(b, cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "stream");
+            std::vector<std::vector<BtcStep>> steps;
+            for (InstHost &h : b->inst) {
+                std::vector<BtcStep> st;
+                h.persistent = persistent_steps(h, &st);
+                if (h.persistent) steps.push_back(std::move(st));
+            }
+            if (!steps.empty()) {
+                if (int rc = tune_persistent(b, steps); rc != RCS_OK) {
+                    std::string m = b->err;
+                    free_batch(b);
+                    return set_thread_error(rc, m);
+                }
+            }
             const size_t nside = std::min<size_t>(64, n_items);
             b->side.resize(nside, nullptr);
             for (auto &s : b->side) BCUDA(b, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "stream");
@@ -683,7 +835,9 @@ int rcs_batch_create(const rcs_batch_item *items, size_t n_items, const rcs_opts
         }
         for (size_t i = 0; i < n_items; ++i) {
             InstHost &h = b->inst[i];
-            h.k = tune ? autotune_k(b, h.n, hg[i], scratch) : std::min(k_fixed, h.n);
+            const Tuned tu = tune ? autotune(b, h.n, hg[i], scratch) : Tuned{std::min(k_fixed, h.n), kSlicesPerItem};
+            h.k = tu.k;
+            h.slices_per_item = tu.slices_per_item;
             h.plan.n = h.n;
             h.plan.precision = RCS_PREC_FP32_FUSED;
             h.plan.k_max = h.k;
@@ -697,7 +851,7 @@ int rcs_batch_create(const rcs_batch_item *items, size_t n_items, const rcs_opts
         for (InstHost &h : b->inst) {
             int kmin = 8;
             for (const Pass &p : h.plan.passes) kmin = std::min(kmin, p.k);
-            h.items_per_pass = h.plan.passes.empty() ? 0 : items_per_pass(h.n, kmin);
+            h.items_per_pass = h.plan.passes.empty() ? 0 : items_per_pass(h.n, kmin, h.slices_per_item);
         }
         std::vector<BPass> passes;
         std::vector<float4> U;
@@ -706,7 +860,8 @@ int rcs_batch_create(const rcs_batch_item *items, size_t n_items, const rcs_opts
         build_tables(b->inst, &passes, &U, &segs, &pass0, &b->nitems);
         std::vector<BInst> binst(n_items);
         for (size_t i = 0; i < n_items; ++i)
-            binst[i] = BInst{b->inst[i].psi, uint32_t(b->inst[i].n), uint32_t(b->inst[i].items_per_pass)};
+            binst[i] = BInst{b->inst[i].psi, uint32_t(b->inst[i].n), uint32_t(b->inst[i].items_per_pass),
+                             b->inst[i].slices_per_item, 0};
         b->nseg = uint32_t(segs.size());
         BCUDA(b, cudaMalloc(&b->d_inst, binst.size() * sizeof(BInst)), "tables");
         BCUDA(b, cudaMalloc(&b->d_pass, std::max<size_t>(passes.size(), 1) * sizeof(BPass)), "tables");
@@ -810,7 +965,7 @@ int rcs_batch_state_read(rcs_batch *b, size_t i, uint64_t first, uint64_t count,
 
 int rcs_batch_set_fault(rcs_batch *b, int64_t skip_item, double wait_limit_s) {
     if (!b) return set_thread_error(RCS_ERR_ARG, "null batch");
-    if (b->tc) return bfail(b, RCS_ERR_UNSUPPORTED, "the tensor-core batch has no work items to fault");
+    if (b->tc && !b->btc) return bfail(b, RCS_ERR_UNSUPPORTED, "no circuit of this batch runs in the persistent kernel");
     int clk_khz = 0;
     cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, b->dev);
     b->skip_item = skip_item;

@@ -140,6 +140,9 @@ int run_substages(const Plan &plan, const std::vector<SubStage> &stages, void *p
 int launch_plan_pass(void *psi, int n, const Pass &p, const uint8_t *ops, int *d_err, void *stream, bool tf32);
 int launch_pass_plain(void *psi, int n, const Pass &p, void *stream);
 int launch_pass_simt(void *psi, int n, const Pass &p, void *stream);
+// Sets the fused SIMT kernels' shared-memory attribute on the current device (once);
+// launch_pass_simt calls it, and a caller about to capture a graph calls it first.
+int simt_prepare_device();
 // Sets the tensor-core kernels' shared-memory attribute on the current device (once);
 // launch_pass_tc calls it, and a caller about to capture a graph calls it first.
 int tc_prepare_device();
@@ -157,6 +160,34 @@ int launch_pass_tc_from_sub(void *psi, int n, const Pass &p, const void *d_ops, 
 // the tile (of CTA 0) whose MMAs are skipped, as every launch reads them, and the setter.
 void tc_test_fault(long long *wait_cycles, int *skip_tile);
 void tc_set_test_fault(int skip_tile, long long wait_cycles);
+
+// Persistent tensor-core kernel of the batched engine (k_batch_tc.cu): every pass of
+// many circuits in one cooperative launch. A step is one 6-qubit tensor-core pass on a
+// state of m qubits (13..30) at dst; its input is dst itself, or a sub-state src whose
+// qubits are tmask (in dst's numbering; the state is |0> on the others), or, with
+// from_zero, the state |0...0>. ops is the pass's operand image (tc_build_ops).
+struct BtcStep {
+    void *dst = nullptr;
+    int m = 0;
+    const void *src = nullptr;
+    int src_m = 0;          // qubits of src (popcount of tmask)
+    uint64_t tmask = 0;
+    bool from_zero = false;
+    const void *ops = nullptr;
+    Pass p;
+};
+struct BtcPlan;
+// Builds the pass and item tables (each pass cut into items of tiles_per_item tiles of
+// 128 slices) on the current device and sets the kernel's shared-memory attribute.
+// Steps of one circuit run in order; circuits are independent. Synchronous.
+int btc_create(const std::vector<std::vector<BtcStep>> &circuits, bool tf32, uint32_t tiles_per_item,
+               BtcPlan **out);
+uint32_t btc_items(const BtcPlan *p);
+// Clears the completion counters and launches the kernel on `stream` (capturable).
+// d_err[0] receives kErrTimeout if a wait ran out; d_err[1] is the launch-wide abort
+// word (0 on entry). skip_item >= 0: that item never publishes its completion (test).
+int btc_launch(const BtcPlan *p, int *d_err, long long wait_cycles, long long skip_item, void *stream);
+void btc_destroy(BtcPlan *p);
 
 // Size in bytes of the operand image of one 6-qubit pass (BF16x3: 64 KB, TF32x3:
 // 96 KB), and its builder.

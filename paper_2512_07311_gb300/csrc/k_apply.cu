@@ -136,11 +136,13 @@ __global__ void __launch_bounds__(256) k_plain_2q(float2 *__restrict__ psi, uint
     }
 }
 
-// Complex matrix entry with its negated imaginary part precomputed on the host, so
-// the mat-vec's multiply-adds take all three as direct constant-bank operands
-// (no negation that the compiler could hoist into registers).
+// Complex matrix entry as the two packed operands of its multiply-adds, precomputed on
+// the host: rr = (re, re) and ni = (-im, im). With (x, y) an input amplitude, the packed
+// FP32x2 fused multiply-adds acc += rr * (x, y) and acc += ni * (y, x) form
+// (acc.x + re x - im y, acc.y + re y + im x): per component the same two fused
+// multiply-adds, in the same order, as four scalar ones, in half the instructions.
 struct CEnt {
-    float re, im, nim;
+    float2 rr, ni;
 };
 
 template <int K>
@@ -206,9 +208,12 @@ __global__ void __launch_bounds__(256, simt_blocks_per_sm<K>()) k_fused_simt(flo
     for (; s < a.slices; s += stride, buf ^= 1) {
         issue(s + stride, buf ^ 1);
         asm volatile("cp.async.wait_group 1;" ::: "memory");  // this slice's copies have landed
-        float2 v[D];
+        float2 v[D], w[D];  // each input and its swapped form (y, x)
 #pragma unroll
-        for (int j = 0; j < D; ++j) v[j] = stage[(buf * D + j) * 256 + threadIdx.x];
+        for (int j = 0; j < D; ++j) {
+            v[j] = stage[(buf * D + j) * 256 + threadIdx.x];
+            w[j] = make_float2(v[j].y, v[j].x);
+        }
         float2 *p = psi + base_of(s);
 #pragma unroll
         for (int j = 0; j < D; ++j) {
@@ -216,10 +221,8 @@ __global__ void __launch_bounds__(256, simt_blocks_per_sm<K>()) k_fused_simt(flo
 #pragma unroll
             for (int l = 0; l < D; ++l) {
                 const CEnt &u = a.U[j][l];
-                acc.x = fmaf(u.re, v[l].x, acc.x);
-                acc.x = fmaf(u.nim, v[l].y, acc.x);
-                acc.y = fmaf(u.re, v[l].y, acc.y);
-                acc.y = fmaf(u.im, v[l].x, acc.y);
+                acc = __ffma2_rn(u.rr, v[l], acc);
+                acc = __ffma2_rn(u.ni, w[l], acc);
             }
             p[offs[j]] = acc;
         }
@@ -318,6 +321,29 @@ int launch_pass_plain(void *psi, int n, const Pass &p, void *stream) {
     return check_launch();
 }
 
+// Shared-memory attribute of k_fused_simt<K> on the current device (once).
+template <int K>
+static int simt_attr() {
+    static bool attr_done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && attr_done[dev]) return RCS_OK;
+    const int smem = 2 * (1 << K) * 256 * int(sizeof(float2));
+    const cudaError_t e = cudaFuncSetAttribute(k_fused_simt<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return note_launch_error("fused kernel shared-memory attribute", e);
+    if (dev >= 0 && dev < 64) attr_done[dev] = true;
+    return RCS_OK;
+}
+
+int simt_prepare_device() {
+    int rc = simt_attr<1>();
+    if (rc == RCS_OK) rc = simt_attr<2>();
+    if (rc == RCS_OK) rc = simt_attr<3>();
+    if (rc == RCS_OK) rc = simt_attr<4>();
+    if (rc == RCS_OK) rc = simt_attr<5>();
+    return rc;
+}
+
 template <int K>
 static int launch_simt_k(float2 *psi, int n, const Pass &p, cudaStream_t st) {
     SimtArgs<K> a;
@@ -325,20 +351,13 @@ static int launch_simt_k(float2 *psi, int n, const Pass &p, cudaStream_t st) {
     for (int j = 0; j < D; ++j)
         for (int l = 0; l < D; ++l) {
             const cd &u = p.U[size_t(j) * D + l];
-            a.U[j][l] = CEnt{float(u.real()), float(u.imag()), -float(u.imag())};
+            a.U[j][l] = CEnt{make_float2(float(u.real()), float(u.real())), make_float2(-float(u.imag()), float(u.imag()))};
         }
     for (int i = 0; i < K; ++i) a.t[i] = p.t[i];
     a.slices = 1ull << (n - K);
     const int threads = 256;
     const int smem = 2 * (1 << K) * threads * int(sizeof(float2));
-    static bool attr_done[5][64] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64 || !attr_done[K - 1][dev]) {
-        const cudaError_t e = cudaFuncSetAttribute(k_fused_simt<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return note_launch_error("fused kernel shared-memory attribute", e);
-        if (dev >= 0 && dev < 64) attr_done[K - 1][dev] = true;
-    }
+    if (int rc = simt_attr<K>(); rc != RCS_OK) return rc;
     // persistent: the resident CTAs, never more than the slices need
     const unsigned grid = grid_for(a.slices, threads, device_sm_count(), simt_blocks_per_sm<K>());
     k_fused_simt<K><<<grid, threads, smem, st>>>(psi, a);

@@ -4,6 +4,7 @@ Same tolerances as the single-circuit tests: infidelity <= 1e-5, max amplitude
 error <= 1e-6, sampler agreement with the oracle sampler on the same state
 >= 99.99%, XEB equal to the oracle's on the same samples to 1e-9."""
 import math
+import time
 
 import numpy as np
 import pytest
@@ -174,8 +175,9 @@ def test_batched_workload_64(lib, oracle):
 @pytest.mark.parametrize("precision", [capi.RCS_PREC_BF16X3, capi.RCS_PREC_TF32X3])
 def test_batch_tensor_core_vs_oracle(lib, oracle, precision):
     """The tensor-core engine: each circuit planned with its own layout and sub-state
-    prefix (12 qubits: the FP32 fallback), states, samples and XEB in the circuit's own
-    qubit numbering."""
+    prefix, the passes of every circuit of 13 or more qubits in the persistent kernel
+    (12 qubits: FP32 fused passes in a launch chain of its own), states, samples and XEB
+    in the circuit's own qubit numbering."""
     circs = small_batch()
     shots = 20_000
     b = capi.rcs_batch_create([(c.n_qubits, c.gates, shots, 40 + i) for i, c in enumerate(circs)],
@@ -195,9 +197,32 @@ def test_batch_tensor_core_vs_oracle(lib, oracle, precision):
             g128 = got.astype(np.complex128)
             assert np.mean(xs == oracle.sample(g128, shots, 40 + i)) >= 0.9999
             assert abs(F - oracle.xeb(g128, xs)) <= 1e-9
+    finally:
+        capi.rcs_batch_destroy(b)
+
+
+@pytest.mark.parametrize("precision", [capi.RCS_PREC_BF16X3, capi.RCS_PREC_TF32X3])
+def test_batch_tensor_core_wait_limit_reports_timeout(lib, oracle, precision):
+    """The persistent tensor-core kernel's bounded waits: a work item that never publishes
+    its completion (everything it issued still completes) makes the next pass of its
+    circuit wait past a short limit; the launch ends with RCS_ERR_TIMEOUT, every CTA stops,
+    and after the hook is cleared a normal launch gives the oracle's states."""
+    circs = small_batch()[1:4]  # 14, 16, 17 qubits: all in the persistent kernel
+    b = capi.rcs_batch_create([(c.n_qubits, c.gates, 1000, 3) for c in circs], precision=precision)
+    try:
+        capi.rcs_batch_set_fault(b, 0, 0.05)
+        t0 = time.perf_counter()
+        capi.rcs_batch_launch(b)
         with pytest.raises(capi.RcsError) as e:
-            capi.rcs_batch_set_fault(b, 0, 0.1)
-        assert e.value.code == capi.RCS_ERR_UNSUPPORTED
+            capi.rcs_batch_wait(b)
+        assert e.value.code == capi.RCS_ERR_TIMEOUT
+        assert time.perf_counter() - t0 < 1.0  # one short limit, not the default
+        capi.rcs_batch_set_fault(b, -1)
+        capi.rcs_batch_launch(b)
+        capi.rcs_batch_wait(b)
+        for i, c in enumerate(circs):
+            got = capi.rcs_batch_state_read(b, i)
+            assert infidelity(got, oracle.simulate(c.n_qubits, c.gates)) <= 1e-5
     finally:
         capi.rcs_batch_destroy(b)
 
