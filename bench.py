@@ -295,9 +295,10 @@ def batch64_measure(args, torch, capi, precision: str):
     stream = torch.cuda.current_stream()
     peaks = measured_peaks()
 
-    def timed(precision):
+    def timed(precision, shots=shots):
         b = capi.rcs_batch_create([(c.n_qubits, c.gates, shots, c.seed) for c in circs], precision=precision)
         infos = [capi.rcs_batch_info(b, i) for i in range(len(circs))]
+        tuning = capi.rcs_batch_tuning(b) if precision != capi.RCS_PREC_FP32_FUSED else None
         for _ in range(args.warmup):
             capi.rcs_batch_launch(b, stream.cuda_stream)
         capi.rcs_batch_wait(b, stream.cuda_stream)
@@ -311,7 +312,7 @@ def batch64_measure(args, torch, capi, precision: str):
         ms = e0.elapsed_time(e1) / args.steps
         xebs = [capi.rcs_batch_result(b, i, 0)[1] for i in range(len(circs))]
         capi.rcs_batch_destroy(b)
-        return ms, infos, xebs
+        return ms, infos, xebs, tuning
 
     def state_bytes(precision, infos):
         """HBM bytes of state construction: passes (the sub-state prefix at its own size), reset/expansion."""
@@ -329,14 +330,17 @@ def batch64_measure(args, torch, capi, precision: str):
         return total
 
     prec = capi.PRECISIONS[precision]
-    ms, infos, xebs = timed(prec)
+    ms, infos, xebs, tuning = timed(prec)
+    # the same batch without shots: its graph is the persistent tensor-core kernel alone
+    # (plus the clear of its counters), so this times state construction by itself
+    ms_apply = timed(prec, shots=0)[0]
     apply_bytes = state_bytes(prec, infos)
     sample_bytes = sum(16.0 * 2**c.n_qubits for c in circs)  # block sums + the sampled blocks, about two reads
-    ms_f, infos_f, xebs_f = timed(capi.RCS_PREC_FP32_FUSED)
+    ms_f, infos_f, xebs_f, _ = timed(capi.RCS_PREC_FP32_FUSED)
     bytes_f = state_bytes(capi.RCS_PREC_FP32_FUSED, infos_f)
     return {"circs": circs, "shots": shots, "ms": ms, "infos": infos, "xebs": xebs, "apply_bytes": apply_bytes,
             "sample_bytes": sample_bytes, "ms_f": ms_f, "infos_f": infos_f, "xebs_f": xebs_f, "bytes_f": bytes_f,
-            "peak": peaks["hbm_gbs"]}
+            "ms_apply": ms_apply, "tuning": tuning, "peak": peaks["hbm_gbs"]}
 
 
 def run_batch(args, torch, capi):
@@ -358,6 +362,13 @@ def run_batch(args, torch, capi):
             "state_plus_sampling_GBps": (apply_bytes + sample_bytes) / (ms / 1e3) / 1e9,
             "frac_of_hbm": (apply_bytes + sample_bytes) / (ms / 1e3) / 1e9 / peaks["hbm_gbs"],
             "xeb_mean": float(np.mean(xebs)), "xeb_min": float(np.min(xebs)), "xeb_max": float(np.max(xebs)),
+            "roofline": {"bound": "hbm", "kernel": "k_batch_tc (all passes of all circuits, one launch)",
+                         "achieved": apply_bytes / (m["ms_apply"] / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
+                         "unit": "GB/s", "frac": apply_bytes / (m["ms_apply"] / 1e3) / 1e9 / peaks["hbm_gbs"],
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)", "traffic": None,
+                         "duration_ms": m["ms_apply"]},
+            "apply_only_s": m["ms_apply"] / 1e3, "sampling_and_xeb_s": (ms - m["ms_apply"]) / 1e3,
+            "tuning": m["tuning"],
             "compare": {"fp32_persistent": {
                 "value": ms_f / 1e3, "k_chosen": [inf["k"] for inf in infos_f],
                 "passes_total": int(sum(inf["n_passes"] for inf in infos_f)), "state_hbm_bytes": bytes_f,
@@ -580,6 +591,9 @@ def main():
         compare["batch64"] = {
             "tensor_core_s": m["ms"] / 1e3, "fp32_persistent_s": m["ms_f"] / 1e3,
             "tensor_core_frac_of_hbm": both / (m["ms"] / 1e3) / 1e9 / m["peak"],
+            "tensor_core_apply_only_s": m["ms_apply"] / 1e3,
+            "tensor_core_apply_frac_of_hbm": m["apply_bytes"] / (m["ms_apply"] / 1e3) / 1e9 / m["peak"],
+            "tiles_per_item": m["tuning"]["tiles_per_item"] if m["tuning"] else None,
             "fp32_frac_of_hbm": (m["bytes_f"] + m["sample_bytes"]) / (m["ms_f"] / 1e3) / 1e9 / m["peak"],
             "xeb_mean_tensor_core": float(np.mean(m["xebs"])), "steps": args.steps}
     if rank == 0:

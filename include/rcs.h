@@ -375,6 +375,14 @@ int rcs_batch_wait(rcs_batch *batch, uint64_t stream);
 int rcs_batch_size(const rcs_batch *batch);
 int rcs_batch_info(const rcs_batch *batch, size_t i, int32_t *n_qubits, int32_t *k, int64_t *n_passes);
 
+/* Tensor-core engine: the work-item size of the persistent kernel (tiles of 128 slices
+ * per item) that the timed trials at creation chose, and each candidate's trial time
+ * (ms per launch of the kernel alone, HOST doubles, candidates 2, 4, 8, 16 and 32 tiles
+ * in that order; 0 for a candidate not tried). Either pointer may be NULL.
+ * RCS_ERR_UNSUPPORTED when no circuit of the batch runs in the persistent kernel (the
+ * FP32 engine, or only circuits under 13 qubits). */
+int rcs_batch_tuning(const rcs_batch *batch, uint32_t *tiles_per_item, double *trial_ms);
+
 /* Copies circuit i's samples (shots uint64, HOST) and XEB (HOST double) of the last
  * completed launch; either pointer may be NULL. Synchronous. */
 int rcs_batch_result(rcs_batch *batch, size_t i, uint64_t *out_bits, double *out_xeb);

@@ -104,6 +104,7 @@ SIGNATURES = [
     ("rcs_batch_state_read", ctypes.c_int, [_P, ctypes.c_size_t, ctypes.c_uint64, ctypes.c_uint64, _f32p]),
     ("rcs_batch_set_fault", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double]),
     ("rcs_batch_last_error", ctypes.c_char_p, [_P]),
+    ("rcs_batch_tuning", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_double)]),
     ("rcs_batch_destroy", None, [_P]),
     ("rcs_batch_run", ctypes.c_int, [ctypes.POINTER(rcs_grid), ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_size_t),
                                      ctypes.c_size_t, _u64p, _u64p, ctypes.POINTER(_u64p), _f64p,
@@ -400,6 +401,15 @@ def rcs_batch_info(batch, i: int) -> dict:
     n, k, p = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
     _check(load().rcs_batch_info(batch, i, ctypes.byref(n), ctypes.byref(k), ctypes.byref(p)))
     return {"n_qubits": n.value, "k": k.value, "n_passes": p.value}
+
+
+def rcs_batch_tuning(batch) -> dict:
+    """The persistent tensor-core kernel's chosen tiles per work item and the trial time of
+    each candidate (ms per launch)."""
+    g = ctypes.c_uint32()
+    ms = (ctypes.c_double * 5)()
+    _check(load().rcs_batch_tuning(batch, ctypes.byref(g), ms))
+    return {"tiles_per_item": g.value, "trial_ms": dict(zip((2, 4, 8, 16, 32), list(ms)))}
 
 
 def rcs_batch_result(batch, i: int, shots: int):

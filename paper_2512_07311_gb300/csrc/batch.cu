@@ -33,6 +33,7 @@
 #include <bit>
 #include <chrono>
 #include <cmath>
+#include <iterator>
 #include <map>
 #include <mutex>
 #include <new>
@@ -240,6 +241,7 @@ struct rcs_batch {
     bool tc = false;  // tensor-core engine
     BtcPlan *btc = nullptr;        // tensor-core engine: the persistent kernel's tables
     uint32_t tiles_per_item = 0;   // ... and their chosen item size
+    double trial_ms[5] = {0, 0, 0, 0, 0};  // the trials (candidates kTilesPerItem)
     std::vector<InstHost> inst;
     BInst *d_inst = nullptr;
     BPass *d_pass = nullptr;
@@ -623,7 +625,8 @@ int tune_persistent(rcs_batch *b, const std::vector<std::vector<BtcStep>> &steps
     BCUDA(b, cudaEventCreate(&e1), "event");
     float best_ms = 0.f;
     int rc = RCS_OK;
-    for (uint32_t g : kTilesPerItem) {
+    for (size_t gi = 0; gi < std::size(kTilesPerItem); ++gi) {
+        const uint32_t g = kTilesPerItem[gi];
         BtcPlan *pl = nullptr;
         if ((rc = btc_create(steps, tf32, g, &pl)) != RCS_OK) break;
         float ms = 0.f;
@@ -640,6 +643,7 @@ int tune_persistent(rcs_batch *b, const std::vector<std::vector<BtcStep>> &steps
             btc_destroy(pl);
             break;
         }
+        b->trial_ms[gi] = double(ms) / 3.0;
         if (!b->btc || ms < best_ms) {
             btc_destroy(b->btc);
             b->btc = pl;
@@ -925,6 +929,15 @@ int rcs_batch_info(const rcs_batch *b, size_t i, int32_t *n_qubits, int32_t *k, 
     if (n_qubits) *n_qubits = b->inst[i].n;
     if (k) *k = b->inst[i].k;
     if (n_passes) *n_passes = int64_t(b->inst[i].plan.passes.size());
+    return RCS_OK;
+}
+
+int rcs_batch_tuning(const rcs_batch *b, uint32_t *tiles_per_item, double *trial_ms) {
+    if (!b) return set_thread_error(RCS_ERR_ARG, "null batch");
+    if (!b->btc) return set_thread_error(RCS_ERR_UNSUPPORTED, "no circuit of this batch runs in the persistent kernel");
+    if (tiles_per_item) *tiles_per_item = b->tiles_per_item;
+    if (trial_ms)
+        for (int i = 0; i < 5; ++i) trial_ms[i] = b->trial_ms[i];
     return RCS_OK;
 }
 

@@ -371,14 +371,16 @@ __global__ void __launch_bounds__(256) k_sample_order(const uint64_t *__restrict
 }
 
 // smap: caller index -> stored index (identity: the plain contiguous block reads).
-// Each CTA takes one contiguous range of positions and its warps step through it
-// together (warp w: positions start + w, start + w + 8, ...), so the blocks in flight on
-// an SM at any moment are neighbours in stored order and share their cache lines while
-// these are still in L1/L2; a grid-stride assignment let the warps drift apart by far
-// more than the lifetime of a line in L2.
-// Per shot: lane l sums its 32 caller offsets 32 l .. 32 l + 31 of the block, a warp
-// scan finds the lane L whose range crosses the target, then the 32 lanes load one
-// amplitude each of L's range and a second scan finds the index.
+// Each warp takes one contiguous range of positions (the positions of a CTA's warps are
+// adjacent ranges), so consecutive shots of a warp are in the same or neighbouring
+// blocks in stored order, whose cache lines it has just read; a grid-stride assignment
+// let the warps drift apart by far more than the lifetime of a line in L2.
+// Per block: lane l sums its 32 caller offsets 32 l .. 32 l + 31 of the block (exact
+// fixed-point terms) and the warp scans the 32 sums. Per shot: a ballot on that scan
+// finds the lane L whose range crosses the target, then the 32 lanes load one amplitude
+// each of L's range and a second scan finds the index. Consecutive shots of a warp in
+// the same block keep the block's lane sums, so a block's 1024 amplitudes are summed
+// once per warp, not once per shot (the sums are exact: the same index either way).
 __global__ void __launch_bounds__(256) k_sample_resolve(const float2 *__restrict__ psi, int blog2,
                                                          const uint64_t *__restrict__ bpre,
                                                          const uint64_t *__restrict__ total, uint64_t first,
@@ -416,21 +418,24 @@ __global__ void __launch_bounds__(256) k_sample_resolve(const float2 *__restrict
             if (((32u * uint32_t(lane)) >> q) & 1u) lmap |= 1ull << smap.to[q];
         __syncthreads();
     }
-    const uint64_t per = (shots + gridDim.x - 1) / gridDim.x;
-    const uint64_t beg = uint64_t(blockIdx.x) * per;
+    const uint64_t nwarps = uint64_t(gridDim.x) * nw;
+    const uint64_t per = (shots + nwarps - 1) / nwarps;
+    const uint64_t beg = (uint64_t(blockIdx.x) * nw + (threadIdx.x >> 5)) * per;
     const uint64_t end = beg + per < shots ? beg + per : shots;
     const int Lmax = int((bamps - 1u) >> 5);  // last lane that owns offsets (blocks hold <= 1024)
-    for (uint64_t r = beg; r < end; r += nw) {  // same trip count in every warp: the barrier below
-        const uint64_t i = r + (threadIdx.x >> 5);
-        if (i < end) {
-            const uint64_t sb = order[i];
-            const uint64_t s = sb & 0xffffffffull, b = sb >> 32;
-            uint64_t rhi, rlo;
-            shot_target(first + s, seed, T, rhi, rlo);
-            const uint64_t base = bpre[b];
-            const uint32_t a0 = uint32_t(lane) * 32u;
-            uint64_t ls = 0;
-            const float2 *lb;  // layout: the block's stored base; identity: the block itself
+    const uint32_t a0 = uint32_t(lane) * 32u;
+    uint64_t cur_b = ~0ull;       // block whose lane sums are held
+    uint64_t base = 0, ls = 0, incl = 0;
+    const float2 *lb = psi;       // layout: the block's stored base; identity: the block itself
+    for (uint64_t i = beg; i < end; ++i) {
+        const uint64_t sb = order[i];
+        const uint64_t s = sb & 0xffffffffull, b = sb >> 32;
+        uint64_t rhi, rlo;
+        shot_target(first + s, seed, T, rhi, rlo);
+        if (b != cur_b) {
+            cur_b = b;
+            base = bpre[b];
+            ls = 0;
             if (!smap.identity) {  // blog2 = 10: every lane owns 32 caller offsets
                 lb = psi + (btab[0][b & 63u] | btab[1][(b >> 6) & 63u] | btab[2][(b >> 12) & 63u] |
                             btab[3][(b >> 18) & 63u]);
@@ -445,26 +450,25 @@ __global__ void __launch_bounds__(256) k_sample_resolve(const float2 *__restrict
                     ls += fx_sq(v.x, seen) + fx_sq(v.y, seen) + fx_sq(v.z, seen) + fx_sq(v.w, seen);
                 }
             }
-            uint64_t incl = warp_incl_scan_u64(ls, lane);
-            const unsigned hit = __ballot_sync(0xffffffffu, above(base + incl, rhi, rlo));
-            const int L = hit ? __ffs(hit) - 1 : Lmax;  // hit != 0: lane 31's prefix is the block's inclusive prefix
-            const uint64_t run0 = __shfl_sync(0xffffffffu, base + incl - ls, L);  // prefix before L's range
-            // lane j takes caller offset 32 L + j
-            const uint32_t aL = uint32_t(L) * 32u;
-            uint64_t v = 0;
-            if (!smap.identity) {
-                const uint64_t lmL = __shfl_sync(0xffffffffu, lmap, L);
-                v = fx_amp(__ldg(lb + (lmL | emap[lane])), seen);
-            } else if (aL + uint32_t(lane) < bamps) {
-                v = fx_amp(__ldg(lb + aL + uint32_t(lane)), seen);
-            }
-            incl = warp_incl_scan_u64(v, lane);
-            const unsigned hit2 = __ballot_sync(0xffffffffu, above(run0 + incl, rhi, rlo));
-            const uint32_t cntL = bamps - aL < 32u ? bamps - aL : 32u;
-            const uint32_t j = hit2 ? uint32_t(__ffs(hit2) - 1) : cntL - 1;
-            if (lane == 0) out[s] = (b << blog2) + aL + j;
+            incl = warp_incl_scan_u64(ls, lane);
         }
-        __syncthreads();  // keeps the CTA's warps on neighbouring positions
+        const unsigned hit = __ballot_sync(0xffffffffu, above(base + incl, rhi, rlo));
+        const int L = hit ? __ffs(hit) - 1 : Lmax;  // hit != 0: lane 31's prefix is the block's inclusive prefix
+        const uint64_t run0 = __shfl_sync(0xffffffffu, base + incl - ls, L);  // prefix before L's range
+        // lane j takes caller offset 32 L + j
+        const uint32_t aL = uint32_t(L) * 32u;
+        uint64_t v = 0;
+        if (!smap.identity) {
+            const uint64_t lmL = __shfl_sync(0xffffffffu, lmap, L);
+            v = fx_amp(__ldg(lb + (lmL | emap[lane])), seen);
+        } else if (aL + uint32_t(lane) < bamps) {
+            v = fx_amp(__ldg(lb + aL + uint32_t(lane)), seen);
+        }
+        const uint64_t incl2 = warp_incl_scan_u64(v, lane);
+        const unsigned hit2 = __ballot_sync(0xffffffffu, above(run0 + incl2, rhi, rlo));
+        const uint32_t cntL = bamps - aL < 32u ? bamps - aL : 32u;
+        const uint32_t j = hit2 ? uint32_t(__ffs(hit2) - 1) : cntL - 1;
+        if (lane == 0) out[s] = (b << blog2) + aL + j;
     }
 }
 
