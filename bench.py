@@ -33,7 +33,9 @@ METRIC = "34q 20-cycle circuit time (s), shots/s; fused-TC vs plain FP32 at 1e-5
 # full passes on a 2^27-amplitude state (mean per launch: BF16x3 2.0854 GB, TF32x3 2.0852 GB); the
 # traffic of a pass is proportional to the state size, so a launch at n qubits moves this x 2^n.
 TC_DRAM_BYTES_PER_AMP = {"bf16x3": 2.0854e9 / 2**27, "tf32x3": 2.0852e9 / 2**27}
-PAIR_DRAM_BYTES_PER_AMP = None  # the two-unitary kernel: not yet captured
+PAIR_DRAM_BYTES_PER_AMP = (1.074e9 + 1.012e9) / 2**27  # the two-unitary kernel, captured at 27 qubits
+# the persistent batch kernel on the 64-circuit workload: DRAM bytes of one launch (ncu)
+BATCH64_TC_DRAM_BYTES = 86.469e9 + 92.177e9
 WORKLOAD = "34q_5x7m1_20cyc"
 
 
@@ -343,6 +345,70 @@ def batch64_measure(args, torch, capi, precision: str):
             "ms_apply": ms_apply, "tuning": tuning, "peak": peaks["hbm_gbs"]}
 
 
+def config_measure(args, torch, capi, name: str):
+    """One of the other single-circuit workloads, timed in the default run: the BF16x3 step
+    (reset, passes, shots, XEB) over the run's warm-up and timed steps, and one apply of each
+    other path (TF32x3, fused FP32 k = 4, plain FP32 per gate) from |0...0>, with their subset
+    infidelities against the fused FP32 state (seeded 2^20 amplitudes, as for the headline)."""
+    circ = C.config_circuit(name)
+    n = circ.n_qubits
+    shots = C.CONFIGS[name]["shots"]
+    stream = torch.cuda.current_stream()
+    peaks = measured_peaks()
+    ctx = capi.rcs_create(circ.grid, capi.RCS_PREC_BF16X3, stream=stream.cuda_stream)
+    out = {"qubits": n, "shots": shots, "gates": len(circ.gates)}
+    try:
+        d_bits = torch.empty(shots, dtype=torch.int64, device="cuda")
+        d_xeb = torch.empty(1, dtype=torch.float64, device="cuda")
+        rng = np.random.default_rng(2**20)
+        subset = np.unique(rng.integers(0, 1 << n, size=min(1 << 20, 1 << n), dtype=np.uint64))
+        amps = {}
+        arms = [("bf16x3", capi.RCS_PREC_BF16X3, 0), ("tf32x3", capi.RCS_PREC_TF32X3, 0),
+                ("fp32_fused_k4", capi.RCS_PREC_FP32_FUSED, 4), ("fp32_plain", capi.RCS_PREC_FP32_PLAIN, 0)]
+        for arm, prec, kmax in arms:
+            plan = capi.rcs_plan_build(n, circ.gates, prec, kmax)
+            info = capi.rcs_plan_info(plan)
+            capi.rcs_plan_upload(ctx, plan)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+            def run(seed, sample):
+                ev[0].record(stream)
+                capi.rcs_reset(ctx)
+                capi.rcs_plan_run(ctx, plan)
+                ev[1].record(stream)
+                if sample:
+                    capi.rcs_sample_device(ctx, shots, seed, d_bits.data_ptr())
+                    capi.rcs_xeb_device(ctx, d_bits.data_ptr(), shots, d_xeb.data_ptr())
+                ev[2].record(stream)
+                stream.synchronize()
+                return ev[0].elapsed_time(ev[1]), ev[0].elapsed_time(ev[2])
+
+            reps = args.steps if arm == "bf16x3" else 1
+            warm = args.warmup if arm != "fp32_plain" else 0
+            for w in range(warm):
+                run(1000 + w, arm == "bf16x3")
+            times = [run(s, arm == "bf16x3") for s in range(reps)]
+            capi.rcs_sync(ctx)
+            apply_s = statistics.median(t[0] for t in times) / 1e3
+            rec = {"apply_s": apply_s, "passes": int(info["n_passes"]),
+                   "hbm_frac": info["zero_hbm_bytes"] / apply_s / 1e9 / peaks["hbm_gbs"]}
+            if arm == "bf16x3":
+                rec["step_s"] = statistics.median(t[1] for t in times) / 1e3
+                rec["xeb"] = float(d_xeb.item())
+                rec["prefix_passes_on_substate"] = int(info["prefix_passes"])
+            amps[arm] = capi.rcs_amplitudes(ctx, subset)
+            out[arm] = rec
+            capi.rcs_plan_destroy(plan)
+        ref = amps["fp32_fused_k4"]
+        out["subset_infidelity_vs_fp32_fused_k4"] = {
+            k: float(1.0 - abs(np.vdot(amps[k], ref)) ** 2 / (np.vdot(amps[k], amps[k]).real * np.vdot(ref, ref).real))
+            for k in amps if k != "fp32_fused_k4"}
+        out["speedup_bf16x3_vs_fp32_plain"] = out["fp32_plain"]["apply_s"] / out["bf16x3"]["apply_s"]
+    finally:
+        capi.rcs_destroy(ctx)
+    return out
+
+
 def run_batch(args, torch, capi):
     """The 64-circuit batched workload as its own JSON line: the tensor-core engine is the
     line's value, the persistent FP32 engine is in `compare`."""
@@ -365,7 +431,8 @@ def run_batch(args, torch, capi):
             "roofline": {"bound": "hbm", "kernel": "k_batch_tc (all passes of all circuits, one launch)",
                          "achieved": apply_bytes / (m["ms_apply"] / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
                          "unit": "GB/s", "frac": apply_bytes / (m["ms_apply"] / 1e3) / 1e9 / peaks["hbm_gbs"],
-                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)", "traffic": None,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)", "traffic": BATCH64_TC_DRAM_BYTES,
+                         "traffic_src": "ncu capture of one launch on this workload (dram read + write)",
                          "duration_ms": m["ms_apply"]},
             "apply_only_s": m["ms_apply"] / 1e3, "sampling_and_xeb_s": (ms - m["ms_apply"]) / 1e3,
             "tuning": m["tuning"],
@@ -596,6 +663,9 @@ def main():
             "tiles_per_item": m["tuning"]["tiles_per_item"] if m["tuning"] else None,
             "fp32_frac_of_hbm": (m["bytes_f"] + m["sample_bytes"]) / (m["ms_f"] / 1e3) / 1e9 / m["peak"],
             "xeb_mean_tensor_core": float(np.mean(m["xebs"])), "steps": args.steps}
+        # the other single-circuit workloads (12, 30 and 32 qubits), timed in the same run
+        compare["configs"] = {name: config_measure(args, torch, capi, name)
+                              for name in ("12q_3x4_8cyc", "30q_5x6_14cyc", "32q_4x8_20cyc")}
     if rank == 0:
         line = {
             "metric": METRIC, "value": per_circuit_seconds(ms_step, world), "unit": "s", "n_gpus": world,
