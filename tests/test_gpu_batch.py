@@ -252,3 +252,36 @@ def test_batched_workload_64_tensor_core(lib, oracle):
         assert checked >= 3
     finally:
         capi.rcs_batch_destroy(b)
+
+
+def test_batch_tensor_core_edge_cases(lib, oracle):
+    """Persistent tensor-core engine at its edges, in one batch: a 13-qubit circuit (one tile,
+    items of one tile), a circuit with no gates (|0...0>: not a persistent-kernel circuit, it
+    runs as its own chain), circuits without shots next to ones with shots, and a 14-qubit
+    circuit whose first pass reads |0...0> directly (a sub-state would have under 13 qubits)."""
+    circs = [C.generate(C.grid_for_n(13), 8, "ABCDCDAB", seed=71),
+             C.generate(C.grid_for_n(14), 9, "EFGH", seed=72, jitter=0.05),
+             C.generate(C.grid_for_n(18), 10, "ABCDCDAB", seed=73)]
+    items = [(circs[0].n_qubits, circs[0].gates, 0, 1), (circs[1].n_qubits, circs[1].gates, 4000, 2),
+             (14, np.zeros(0, dtype=C.GATE_DTYPE), 500, 3), (circs[2].n_qubits, circs[2].gates, 0, 4)]
+    b = capi.rcs_batch_create(items, precision=capi.RCS_PREC_BF16X3)
+    try:
+        tuning = capi.rcs_batch_tuning(b)
+        assert tuning["tiles_per_item"] in (2, 4, 8, 16, 32)
+        for _ in range(2):
+            capi.rcs_batch_launch(b)
+            capi.rcs_batch_wait(b)
+        for i, c in [(0, circs[0]), (1, circs[1]), (3, circs[2])]:
+            got = capi.rcs_batch_state_read(b, i)
+            want = oracle.simulate(c.n_qubits, c.gates)
+            assert infidelity(got, want) <= 1e-5
+            assert np.abs(got - want).max() <= 1e-6
+        zero = capi.rcs_batch_state_read(b, 2)
+        assert zero[0] == 1 and np.count_nonzero(zero) == 1
+        xs, F = capi.rcs_batch_result(b, 2, 500)
+        assert (xs == 0).all() and abs(F - ((1 << 14) - 1)) <= 1e-9  # XEB of a basis state: 2^n - 1
+        xs, F = capi.rcs_batch_result(b, 1, 4000)
+        g128 = capi.rcs_batch_state_read(b, 1).astype(np.complex128)
+        assert np.mean(xs == oracle.sample(g128, 4000, 2)) >= 0.9999
+    finally:
+        capi.rcs_batch_destroy(b)
