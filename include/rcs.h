@@ -332,7 +332,8 @@ int rcs_xeb_device(rcs_ctx *ctx, const uint64_t *d_samples, size_t n, double *d_
 /* Many independent circuits (different qubit counts and depths) run together: one
  * persistent kernel applies every fused pass of every circuit, then each circuit is
  * sampled and scored; the whole sequence is one captured CUDA graph, replayed by
- * rcs_batch_launch. This is the many-instance form of Section 3.2 items 1, 3, 4. */
+ * rcs_batch_launch. This is the many-instance form of Section 3.2 items 1, 3, 4 (the
+ * paper's jobs, Section 4.3). */
 typedef struct rcs_batch rcs_batch;
 
 /* One circuit of a batch: n_qubits (2..30), its host gate list (validated and
@@ -355,9 +356,11 @@ typedef struct {
  *     the batched kernel choose it per qubit count, cached for the process.
  *   BF16X3 or TF32X3: every circuit is planned like rcs_apply_circuit on a fresh
  *     state (fused 6-qubit tensor-core passes, its own qubit layout and sub-state
- *     prefix; circuits under 13 qubits get FP32 fused passes). The graph holds one
- *     chain of launches per circuit on up to 64 parallel branches. opts->k_max must
- *     be 0 or 6.
+ *     prefix). Every pass of every circuit of 13 or more qubits is a work item of one
+ *     cooperative persistent tensor-core launch; the tiles per work item are chosen by
+ *     timed launches of that kernel on the batch at creation (rcs_batch_tuning).
+ *     Circuits under 13 qubits (FP32 fused passes), or with no gates, run as launch
+ *     chains of their own before it. opts->k_max must be 0 or 6.
  * Samples, XEB and rcs_batch_state_read use each circuit's own qubit numbering in
  * either engine. */
 int rcs_batch_create(const rcs_batch_item *items, size_t n_items, const rcs_opts *opts, rcs_batch **out);
@@ -390,11 +393,13 @@ int rcs_batch_result(rcs_batch *batch, size_t i, uint64_t *out_bits, double *out
 /* Copies amplitudes [first, first+count) of circuit i's state to host floats. */
 int rcs_batch_state_read(rcs_batch *batch, size_t i, uint64_t first, uint64_t count, float *out_re_im);
 
-/* Test hook for the bounded waits of the persistent FP32 engine: work item
- * skip_item (>= 0) never publishes its completion, so the passes after it wait until
- * wait_limit_s and the launch ends with RCS_ERR_TIMEOUT; skip_item = -1 restores
- * normal operation (limit ~2 s by default). Recaptures the graph. The tensor-core
- * engine has no work items: RCS_ERR_UNSUPPORTED. */
+/* Test hook for the bounded waits of either persistent engine: work item skip_item
+ * (>= 0; the FP32 kernel's items, or the persistent tensor-core kernel's) never
+ * publishes its completion, so the passes after it wait until wait_limit_s and the
+ * launch ends with RCS_ERR_TIMEOUT; skip_item = -1 restores normal operation (limit
+ * ~2 s by default). Everything the item issued still completes. Recaptures the graph.
+ * RCS_ERR_UNSUPPORTED for a tensor-core batch none of whose circuits runs in the
+ * persistent kernel. */
 int rcs_batch_set_fault(rcs_batch *batch, int64_t skip_item, double wait_limit_s);
 
 /* Last error message of the batch. */

@@ -1,6 +1,6 @@
 // Batched mode: many independent circuits, of different qubit counts and depths,
 // in one persistent kernel launch inside one captured CUDA graph, with the fusion
-// width of every circuit chosen by timed trials.
+// width and work-item size chosen by timed trials.
 //
 // Work items. Each circuit i is planned (FP32 fused, k <= 5) into passes; each pass
 // is cut into items of a few thousand slices. The host lays the items out in rounds
@@ -20,13 +20,14 @@
 // after seeing the count.
 //
 // Tensor-core engine (precision BF16X3 or TF32X3). Each circuit is planned like a
-// single one (fused 6-qubit passes, its own qubit layout and sub-state prefix), and the
-// graph holds one chain of launches per circuit -- reset or prefix and expansion, the
-// tensor-core passes, then the sampler and XEB -- on up to 64 parallel branches. A
-// tensor-core pass needs a whole SM (one 17-warp CTA with ~200 KB of shared memory
-// and 512 tensor-memory columns), so the passes of different circuits cannot share one
-// persistent kernel the way the FP32 items do; the graph's branches let the passes of
-// small circuits run side by side on the SMs the large ones leave free.
+// single one (fused 6-qubit passes, its own qubit layout and sub-state prefix). Every
+// pass of every circuit of 13 or more qubits is then a work item of one cooperative
+// launch of the persistent tensor-core kernel (k_batch_tc.cu: tile ranges of one pass,
+// ordered by per-circuit completion counters; the sub-state stages' zero fill and
+// expansions folded into passes that read a sub-state). The tiles per item are chosen
+// at creation by timed launches of that kernel on the batch itself. Circuits it cannot
+// run (under 13 qubits, or with no gates) go first as launch chains of their own; after
+// the kernel, every circuit's sampler and XEB run on parallel branches of the graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
