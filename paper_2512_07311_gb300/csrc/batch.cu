@@ -79,6 +79,7 @@ struct BArgs {
     const float4 *U;
     const BSeg *seg;
     uint32_t nseg;
+    const uint32_t *item_seg;  // segment of each item
     uint64_t nitems;
     unsigned long long *next_item;
     unsigned int *done;  // per instance: items completed
@@ -118,49 +119,64 @@ __device__ __forceinline__ void apply_items(float2 *__restrict__ psi, const int 
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_batch_apply(const __grid_constant__ BArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) k_batch_apply(const __grid_constant__ BArgs a) {
     __shared__ float4 sU[32 * 32];
     __shared__ uint64_t sOff[32];
     __shared__ unsigned long long s_item;
     __shared__ uint32_t s_seg;
-    __shared__ int s_go;
+    __shared__ int s_go, s_reload;
+    // thread 0 claims the CTA's next item while the CTA works on the current one: the
+    // atomic, the item's segment and a first poll of its circuit's counter are in flight
+    // during the work. Items are still taken in claim order, so a wait is only ever on
+    // items claimed earlier, which no CTA holds back.
+    unsigned long long nxt = 0;
+    uint32_t nxt_seg = 0, cur_pass = ~0u;
+    bool nxt_ready = false;
+    auto claim = [&]() {
+        nxt = *(volatile int *)a.abort_flag ? a.nitems : atomicAdd(a.next_item, 1ull);
+        nxt_ready = false;
+        if (nxt < a.nitems) {
+            nxt_seg = a.item_seg[nxt];
+            const BSeg sg = a.seg[nxt_seg];
+            const unsigned int need = sg.pass_in_inst * a.inst[sg.inst].items_per_pass;
+            nxt_ready = *(const volatile unsigned int *)(a.done + sg.inst) >= need;
+        }
+    };
+    if (threadIdx.x == 0) claim();
     for (;;) {
         if (threadIdx.x == 0) {
-            s_item = *(volatile int *)a.abort_flag ? a.nitems : atomicAdd(a.next_item, 1ull);
+            s_item = nxt;
             s_go = 0;
-            if (s_item < a.nitems) {
-                // segment holding the item: last seg with first_item <= item
-                uint32_t lo = 0, hi = a.nseg - 1;
-                while (lo < hi) {
-                    const uint32_t mid = (lo + hi + 1) >> 1;
-                    if (a.seg[mid].first_item <= s_item) lo = mid;
-                    else hi = mid - 1;
-                }
-                s_seg = lo;
-                const BSeg sg = a.seg[lo];
+            if (nxt < a.nitems) {
+                s_seg = nxt_seg;
+                const BSeg sg = a.seg[nxt_seg];
                 const unsigned int need = sg.pass_in_inst * a.inst[sg.inst].items_per_pass;
                 const volatile unsigned int *done = a.done + sg.inst;
                 const long long t0 = clock64();
                 s_go = 1;
-                while (*done < need) {
-                    if (*(volatile int *)a.abort_flag) {
-                        s_go = 0;
-                        break;
+                if (!nxt_ready)
+                    while (*done < need) {
+                        if (*(volatile int *)a.abort_flag) {
+                            s_go = 0;
+                            break;
+                        }
+                        if (clock64() - t0 > a.wait_cycles) {
+                            atomicOr(a.err, kErrTimeout);
+                            atomicExch(a.abort_flag, 1);
+                            s_go = 0;
+                            break;
+                        }
+                        __nanosleep(200);
                     }
-                    if (clock64() - t0 > a.wait_cycles) {
-                        atomicOr(a.err, kErrTimeout);
-                        atomicExch(a.abort_flag, 1);
-                        s_go = 0;
-                        break;
-                    }
-                    __nanosleep(200);
-                }
                 __threadfence();
+                s_reload = sg.pass != cur_pass;
+                cur_pass = sg.pass;
             }
         }
         __syncthreads();
         if (s_item >= a.nitems) break;
         if (!s_go) {
+            if (threadIdx.x == 0) claim();  // sees the abort flag: the loop ends
             __syncthreads();
             continue;
         }
@@ -168,14 +184,17 @@ __global__ void __launch_bounds__(kThreads) k_batch_apply(const __grid_constant_
         const BInst in = a.inst[sg.inst];
         const BPass ps = a.pass[sg.pass];
         const int D = 1 << ps.k;
-        for (int e = threadIdx.x; e < D * D; e += kThreads) sU[e] = __ldg(a.U + ps.u_off + e);
-        if (threadIdx.x < D) {
-            uint64_t o = 0;
-            for (int i = 0; i < ps.k; ++i)
-                if ((threadIdx.x >> i) & 1) o |= 1ull << ps.t[i];
-            sOff[threadIdx.x] = o;
+        if (s_reload) {  // a new pass: its unitary and target offsets
+            for (int e = threadIdx.x; e < D * D; e += kThreads) sU[e] = __ldg(a.U + ps.u_off + e);
+            if (threadIdx.x < D) {
+                uint64_t o = 0;
+                for (int i = 0; i < ps.k; ++i)
+                    if ((threadIdx.x >> i) & 1) o |= 1ull << ps.t[i];
+                sOff[threadIdx.x] = o;
+            }
+            __syncthreads();
         }
-        __syncthreads();
+        if (threadIdx.x == 0) claim();
         const uint64_t item_in_pass = s_item - sg.first_item;
         const uint64_t nslices = 1ull << (in.n - ps.k);
         const uint64_t s0 = item_in_pass * in.slices_per_item;
@@ -249,6 +268,7 @@ struct rcs_batch {
     float4 *d_U = nullptr;
     BSeg *d_seg = nullptr;
     uint32_t nseg = 0;
+    uint32_t *d_item_seg = nullptr;
     uint64_t nitems = 0;
     unsigned long long *d_next = nullptr;
     unsigned int *d_done = nullptr;
@@ -315,6 +335,17 @@ void build_tables(const std::vector<InstHost> &inst, std::vector<BPass> *passes,
     *nitems = item;
 }
 
+// Segment of every item (items of a segment are consecutive), so the kernel finds an
+// item's pass with one load.
+std::vector<uint32_t> item_segments(const std::vector<BSeg> &segs, uint64_t nitems) {
+    std::vector<uint32_t> out(static_cast<size_t>(nitems));
+    for (size_t i = 0; i < segs.size(); ++i) {
+        const uint64_t end = i + 1 < segs.size() ? segs[i + 1].first_item : nitems;
+        for (uint64_t it = segs[i].first_item; it < end; ++it) out[size_t(it)] = uint32_t(i);
+    }
+    return out;
+}
+
 uint64_t items_per_pass(int n, int k, uint32_t slices_per_item) {
     const uint64_t slices = 1ull << (n - k);
     return (slices + slices_per_item - 1) / slices_per_item;
@@ -327,6 +358,7 @@ int launch_apply(rcs_batch *b, cudaStream_t st, uint64_t nitems) {
     a.U = b->d_U;
     a.seg = b->d_seg;
     a.nseg = b->nseg;
+    a.item_seg = b->d_item_seg;
     a.nitems = nitems;
     a.next_item = b->d_next;
     a.done = b->d_done;
@@ -385,11 +417,13 @@ double time_trial(int n, int k, uint32_t spi, float2 *scratch, rcs_batch *tmpl) 
     std::vector<BSeg> segs;
     std::vector<uint32_t> pass0;
     build_tables(one, &passes, &U, &segs, &pass0, &t.nitems);
+    const std::vector<uint32_t> iseg = item_segments(segs, t.nitems);
     BInst bi{scratch, uint32_t(n), uint32_t(h.items_per_pass), spi, 0};
     double ms = -1.0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaMalloc(&t.d_inst, sizeof(BInst)) == cudaSuccess && cudaMalloc(&t.d_pass, passes.size() * sizeof(BPass)) == cudaSuccess &&
         cudaMalloc(&t.d_U, U.size() * sizeof(float4)) == cudaSuccess && cudaMalloc(&t.d_seg, segs.size() * sizeof(BSeg)) == cudaSuccess &&
+        cudaMalloc(&t.d_item_seg, std::max<size_t>(iseg.size(), 1) * 4) == cudaSuccess &&
         cudaMalloc(&t.d_next, 8) == cudaSuccess && cudaMalloc(&t.d_done, 4) == cudaSuccess && cudaMalloc(&t.d_err, 8) == cudaSuccess &&
         cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
         t.nseg = uint32_t(segs.size());
@@ -397,6 +431,7 @@ double time_trial(int n, int k, uint32_t spi, float2 *scratch, rcs_batch *tmpl) 
         cudaMemcpy(t.d_pass, passes.data(), passes.size() * sizeof(BPass), cudaMemcpyHostToDevice);
         cudaMemcpy(t.d_U, U.data(), U.size() * sizeof(float4), cudaMemcpyHostToDevice);
         cudaMemcpy(t.d_seg, segs.data(), segs.size() * sizeof(BSeg), cudaMemcpyHostToDevice);
+        if (!iseg.empty()) cudaMemcpy(t.d_item_seg, iseg.data(), iseg.size() * 4, cudaMemcpyHostToDevice);
         for (int rep = 0; rep < 2; ++rep) {  // first run warms up
             cudaMemset(t.d_next, 0, 8);
             cudaMemset(t.d_done, 0, 4);
@@ -418,6 +453,7 @@ double time_trial(int n, int k, uint32_t spi, float2 *scratch, rcs_batch *tmpl) 
     cudaFree(t.d_pass);
     cudaFree(t.d_U);
     cudaFree(t.d_seg);
+    cudaFree(t.d_item_seg);
     cudaFree(t.d_next);
     cudaFree(t.d_done);
     cudaFree(t.d_err);
@@ -425,6 +461,7 @@ double time_trial(int n, int k, uint32_t spi, float2 *scratch, rcs_batch *tmpl) 
     t.d_pass = nullptr;
     t.d_U = nullptr;
     t.d_seg = nullptr;
+    t.d_item_seg = nullptr;
     t.d_next = nullptr;
     t.d_done = nullptr;
     t.d_err = nullptr;
@@ -485,6 +522,7 @@ void free_batch(rcs_batch *b) {
     cudaFree(b->d_pass);
     cudaFree(b->d_U);
     cudaFree(b->d_seg);
+    cudaFree(b->d_item_seg);
     cudaFree(b->d_next);
     cudaFree(b->d_done);
     cudaFree(b->d_err);
@@ -880,6 +918,12 @@ int rcs_batch_create(const rcs_batch_item *items, size_t n_items, const rcs_opts
         if (!U.empty()) BCUDA(b, cudaMemcpy(b->d_U, U.data(), U.size() * sizeof(float4), cudaMemcpyHostToDevice), "upload");
         if (!segs.empty())
             BCUDA(b, cudaMemcpy(b->d_seg, segs.data(), segs.size() * sizeof(BSeg), cudaMemcpyHostToDevice), "upload");
+        {
+            const std::vector<uint32_t> iseg = item_segments(segs, b->nitems);
+            BCUDA(b, cudaMalloc(&b->d_item_seg, std::max<size_t>(iseg.size(), 1) * 4), "tables");
+            if (!iseg.empty())
+                BCUDA(b, cudaMemcpy(b->d_item_seg, iseg.data(), iseg.size() * 4, cudaMemcpyHostToDevice), "upload");
+        }
         BCUDA(b, cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "stream");
         const size_t nside = std::min<size_t>(8, n_items);
         b->side.resize(nside, nullptr);
