@@ -182,7 +182,8 @@ def cpu_baseline(circ: C.Circuit, shots: int, budget_s: float = 20.0) -> dict:
     scale = 2.0 ** (n - n_s)
     # sampling = one 2^n CDF pass (dominant) + shots * log2(2^n) searches; scale the pass by 2^(n-n_s)
     est = t_apply * scale * len(circ.gates) / max(done, 1) + t_sample * scale + t_xeb * shots / s_shots
-    return {"value": est, "unit": "s", "cores": O.threads(), "kind": "oracle", "measured": False,
+    whole = n_s == n and done == len(g) and s_shots == shots  # the whole workload ran: no scaling
+    return {"value": est, "unit": "s", "cores": O.threads(), "kind": "oracle", "measured": bool(whole),
             "sample": (f"oracle on a 2^{n_s}-amplitude complex128 state: first {done} of {len(circ.gates)} "
                        f"workload gates (qubit q -> q mod {n_s}), {s_shots} shots + XEB; "
                        f"scaled x2^{n - n_s} per amplitude pass and by gate count"),
@@ -349,7 +350,9 @@ def config_measure(args, torch, capi, name: str):
     """One of the other single-circuit workloads, timed in the default run: the BF16x3 step
     (reset, passes, shots, XEB) over the run's warm-up and timed steps, and one apply of each
     other path (TF32x3, fused FP32 k = 4, plain FP32 per gate) from |0...0>, with their subset
-    infidelities against the fused FP32 state (seeded 2^20 amplitudes, as for the headline)."""
+    infidelities against the fused FP32 state (seeded 2^20 amplitudes, as for the headline),
+    and the CPU oracle on the same workload (whole when it fits the sample, else a bounded
+    sample scaled up)."""
     circ = C.config_circuit(name)
     n = circ.n_qubits
     shots = C.CONFIGS[name]["shots"]
@@ -406,6 +409,9 @@ def config_measure(args, torch, capi, name: str):
         out["speedup_bf16x3_vs_fp32_plain"] = out["fp32_plain"]["apply_s"] / out["bf16x3"]["apply_s"]
     finally:
         capi.rcs_destroy(ctx)
+    if not args.no_cpu:
+        # the CPU oracle on the same workload: whole at 12 qubits, a bounded sample above
+        out["cpu_baseline"] = cpu_baseline(circ, shots, budget_s=8.0)
     return out
 
 
