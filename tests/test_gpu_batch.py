@@ -46,6 +46,9 @@ def test_batch_vs_oracle(lib, oracle, k_max):
         capi.rcs_batch_launch(b)
         capi.rcs_batch_wait(b)
         assert capi.rcs_batch_size(b) == len(circs)
+        with pytest.raises(capi.RcsError) as e:  # the FP32 engine has no persistent tensor-core kernel
+            capi.rcs_batch_tuning(b)
+        assert e.value.code == capi.RCS_ERR_UNSUPPORTED
         for i, c in enumerate(circs):
             info = capi.rcs_batch_info(b, i)
             assert info["n_qubits"] == c.n_qubits and 2 <= info["k"] <= 5
