@@ -76,7 +76,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     return true;
 }
 
-// Warp-uniform bounded wait: lane 0 polls (with the time limit), the verdict is
+// Warp-uniform bounded wait: lane 0 polls (with the time limit), the outcome is
 // broadcast, then every lane performs its own (now immediately successful)
 // acquiring test so the whole warp is ordered after the phase. The phase cannot
 // move on before this warp arrives on its own barrier, so the test cannot miss it.
