@@ -424,9 +424,9 @@ int rcs_batch_run(const rcs_grid *grids, const rcs_gate *const *gates, const siz
 
 /* Linear XEB, as rcs_xeb_device, for callers that cannot allocate device memory:
  * no context is needed and no cudaMalloc, cudaFree or allocating library routine
- * is called. (The paper has no counterpart; this serves callers such as code
- * running while a stream is captured into a CUDA graph, where cudaMalloc is not
- * allowed, or hosts whose device memory comes only from their own arena.)
+ * is called. (The paper has no counterpart; this serves callers such as hosts
+ * whose device memory comes only from their own arena, or that forbid device
+ * allocations after start-up.)
  *
  * d_state: DEVICE, 2^n_qubits complex64 amplitudes (interleaved re, im), 16-byte
  * aligned; d_samples: DEVICE, count uint64 basis indices, 8-byte aligned;
@@ -440,12 +440,12 @@ int rcs_batch_run(const rcs_grid *grids, const rcs_gate *const *gates, const siz
  * every GPU that loads the library holds until the process exits. Hence:
  * count <= 67108864 (2^26) and 1 <= n_qubits <= 34, else RCS_ERR_ARG with a
  * message for rcs_last_error(NULL). The first call on a device looks up the
- * array's device address (with that device current); make that first call
- * before any stream capture. The address is kept for the process: after a
- * cudaDeviceReset() of a device, do not call this entry point on that device
- * again. Devices with ordinals >= 64 get RCS_ERR_UNSUPPORTED. Every call shares the array: calls whose work
- * overlaps on the GPU (other streams, other host threads) race and must be
- * serialised by the caller. */
+ * array's device address (with that device current). The address is kept for
+ * the process: after a cudaDeviceReset() of a device, do not call this entry
+ * point on that device again. Devices with ordinals >= 64 get
+ * RCS_ERR_UNSUPPORTED. Every call shares the array: calls whose work overlaps on
+ * the GPU (other streams, other host threads) race and must be serialised by the
+ * caller. */
 int rcs_xeb_static(const void *d_state, int n_qubits, const uint64_t *d_samples, size_t count, double *d_out_xeb,
                    uint64_t stream);
 

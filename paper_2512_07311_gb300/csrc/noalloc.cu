@@ -1,11 +1,9 @@
 // Linear XEB for callers that cannot allocate device memory.
 //
 // rcs_xeb_device() keeps its partial sums and the norm's block sums in buffers the
-// context allocates with cudaMalloc. Some callers cannot do that: code running
-// while a stream is being captured into a CUDA graph (cudaMalloc is not a
-// capturable operation), code whose memory is handed out by a host framework's
-// own allocator or a fixed arena, and hosts that forbid device allocations after
-// start-up. rcs_xeb_static() computes the same quantity from caller-owned device
+// context allocates with cudaMalloc. Some callers cannot do that: code whose
+// memory is handed out by a host framework's own allocator or a fixed arena, and
+// hosts that forbid device allocations after start-up. rcs_xeb_static() computes the same quantity from caller-owned device
 // buffers only: its scratch is one file-scope __device__ array, fixed in size and
 // held by every GPU that loads this library until the process exits.
 //

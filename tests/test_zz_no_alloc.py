@@ -1,6 +1,6 @@
 """rcs_xeb_static: the allocation-free XEB entry point, for callers that cannot
-call cudaMalloc (for example while a stream is being captured into a CUDA graph,
-or when all device memory comes from the caller's own arena). It must give the
+call cudaMalloc (for example when all device memory comes from the caller's own
+arena). It must give the
 same score as rcs_xeb_device on the same state and samples, call after call,
 although its scratch is one fixed device array shared by every call.
 
