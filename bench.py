@@ -368,6 +368,8 @@ def config_measure(args, torch, capi, name: str):
         amps = {}
         arms = [("bf16x3", capi.RCS_PREC_BF16X3, 0), ("tf32x3", capi.RCS_PREC_TF32X3, 0),
                 ("fp32_fused_k4", capi.RCS_PREC_FP32_FUSED, 4), ("fp32_plain", capi.RCS_PREC_FP32_PLAIN, 0)]
+        if n <= 30:  # the fused FP32 widths 5..7 (6 and 7 bound by the FMA pipe) up to the 30-qubit workload
+            arms[3:3] = [(f"fp32_fused_k{k}", capi.RCS_PREC_FP32_FUSED, k) for k in (5, 6, 7)]
         for arm, prec, kmax in arms:
             plan = capi.rcs_plan_build(n, circ.gates, prec, kmax)
             info = capi.rcs_plan_info(plan)
@@ -387,7 +389,7 @@ def config_measure(args, torch, capi, name: str):
                 return ev[0].elapsed_time(ev[1]), ev[0].elapsed_time(ev[2])
 
             reps = args.steps if arm == "bf16x3" else 1
-            warm = args.warmup if arm != "fp32_plain" else 0
+            warm = args.warmup if arm in ("bf16x3", "tf32x3", "fp32_fused_k4") else (1 if arm != "fp32_plain" else 0)
             for w in range(warm):
                 run(1000 + w, arm == "bf16x3")
             times = [run(s, arm == "bf16x3") for s in range(reps)]
@@ -407,12 +409,49 @@ def config_measure(args, torch, capi, name: str):
             k: float(1.0 - abs(np.vdot(amps[k], ref)) ** 2 / (np.vdot(amps[k], amps[k]).real * np.vdot(ref, ref).real))
             for k in amps if k != "fp32_fused_k4"}
         out["speedup_bf16x3_vs_fp32_plain"] = out["fp32_plain"]["apply_s"] / out["bf16x3"]["apply_s"]
+        if n <= 30 and n >= 20:
+            out["fp32_wide_pass"] = wide_pass_measure(torch, capi, ctx, n, stream)
     finally:
         capi.rcs_destroy(ctx)
     if not args.no_cpu:
         # the CPU oracle on the same workload: whole at 12 qubits, a bounded sample above
         out["cpu_baseline"] = cpu_baseline(circ, shots, budget_s=8.0)
     return out
+
+
+# FP32 FMA peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flop at the 2070 MHz
+# maximum SM clock.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def wide_pass_measure(torch, capi, ctx, n, stream):
+    """One full-state FP32 pass of width 6 and of width 7 (U in shared memory), three
+    timed launches each after one untimed, against the FP32 FMA peak: 8 * 2^k real flop
+    per amplitude."""
+    rng = np.random.default_rng(7)
+    res = {}
+    for k in (6, 7):
+        targets = list(range(5, 5 + k))  # above the 32 slices a warp stores side by side
+        mats = []
+        for _ in range(4):
+            a = rng.normal(size=(1 << k, 1 << k)) + 1j * rng.normal(size=(1 << k, 1 << k))
+            q, r = np.linalg.qr(a)
+            mats.append(q * (np.diag(r) / abs(np.diag(r))))
+        capi.rcs_apply_unitary(ctx, targets, mats[0])
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        for u in mats[1:]:
+            capi.rcs_apply_unitary(ctx, targets, u)
+        ev[1].record(stream)
+        stream.synchronize()
+        ms = ev[0].elapsed_time(ev[1]) / 3
+        flops = 8.0 * 2**k * 2**n
+        res[f"k{k}"] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12,
+                        "alu_frac": flops / (ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+                        "hbm_frac": 16.0 * 2**n / (ms / 1e3) / 1e9 / measured_peaks()["hbm_gbs"]}
+    res["peak_tflops"] = FP32_PEAK_TFLOPS
+    res["peak_source"] = "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (unit counts and maximum clock)"
+    return res
 
 
 def run_batch(args, torch, capi):

@@ -60,7 +60,7 @@ extern "C" {
 
 /* ---- numerical paths for the state update */
 #define RCS_PREC_FP32_PLAIN 0 /* one kernel launch per gate, FP32 SIMT (the baseline path) */
-#define RCS_PREC_FP32_FUSED 1 /* gates fused into k-qubit unitaries (k <= k_max <= 5), FP32 SIMT */
+#define RCS_PREC_FP32_FUSED 1 /* gates fused into k-qubit unitaries (k <= k_max <= 7), FP32 SIMT */
 #define RCS_PREC_BF16X3 2     /* fused 6-qubit unitaries on tcgen05 tensor cores, BF16 hi/lo split, 3 products, FP32 accumulate */
 #define RCS_PREC_TF32X3 3     /* the same passes with a TF32 hi/lo split (3 products, FP32 accumulate): about
                                * 2^-21 relative error per product instead of 2^-17, at half the tensor rate */
@@ -87,8 +87,10 @@ typedef struct {
     const double *u;
 } rcs_gate;
 
-/* Options. precision: RCS_PREC_*. k_max: largest fused block (FP32_FUSED: 2..5,
- * default 4; BF16X3 and TF32X3: 6). autotune: 1 = for FP32_FUSED, rcs_apply_circuit chooses
+/* Options. precision: RCS_PREC_*. k_max: largest fused block (FP32_FUSED: 2..7,
+ * default 4; widths 6 and 7 multiply each tile of 64 slices by U in shared memory and
+ * are bound by the FP32 FMA pipe, at 32 and 64 flop per byte; BF16X3 and TF32X3: 6).
+ * autotune: 1 = for FP32_FUSED, rcs_apply_circuit chooses
  * k_max in 2..5 minimising (passes at width k) x (measured time of a width-k pass
  * on this state), by timed trial passes on the first call for this qubit count on
  * this device (cached for the process; the trials leave the state bit-identical).
@@ -179,15 +181,15 @@ int rcs_reset(rcs_ctx *ctx);
  * layout (at most five exact swap passes). rcs_qubit_layout reports it. */
 int rcs_apply_circuit(rcs_ctx *ctx, const rcs_gate *gates, size_t n_gates);
 
-/* Applies one dense k-qubit unitary (1 <= k <= 6) to targets[0..k-1] (distinct,
+/* Applies one dense k-qubit unitary (1 <= k <= 7) to targets[0..k-1] (distinct,
  * local index j = sum_i bit(targets[i]) 2^i); u_re_im holds 2^k x 2^k complex128
- * entries, row-major, interleaved, unitary to 1e-6. k <= 5 runs the FP32 fused
- * kernel; k = 6 needs the BF16X3 or TF32X3 precision and n >= 13 (tensor-core kernel),
- * else RCS_ERR_UNSUPPORTED. Asynchronous. */
+ * entries, row-major, interleaved, unitary to 1e-6. k = 6 with the BF16X3 or TF32X3
+ * precision on n >= 13 runs the tensor-core kernel; every other k runs the FP32
+ * fused kernels (k = 6, 7: U in shared memory). Asynchronous. */
 int rcs_apply_unitary(rcs_ctx *ctx, int k, const int32_t *targets, const double *u_re_im);
 
 /* Applies count dense unitaries in order (psi <- U_{count-1} ... U_0 psi), each as
- * rcs_apply_unitary would: unitary i has k[i] targets (1..6), listed in targets at
+ * rcs_apply_unitary would: unitary i has k[i] targets (1..7), listed in targets at
  * offset k[0] + ... + k[i-1], and its 2^k x 2^k complex128 matrix (row-major,
  * interleaved) at u_re_im[i]. All are validated before anything runs (a rejected
  * list leaves the state unchanged). With BF16X3 on n >= 13 qubits and

@@ -141,7 +141,9 @@ int valid_gates(rcs_ctx *ctx, int n, const rcs_gate *gates, size_t count, std::v
 
 // ---- autotuner for the fused FP32 path: k_max in 2..5 minimising
 // (passes of the circuit at width k) x (measured time of one width-k pass on this
-// state), cached per (device, qubit count). The trial passes are phase permutations
+// state), cached per (device, qubit count). Widths 6 and 7 are not tried: at 32 and
+// 64 flop per byte their passes are bound by the FP32 FMA pipe, several times longer
+// than a round trip through HBM, while they cut the passes by far less. The trial passes are phase permutations
 // (entries 0 and i): FP32 multiply-adds apply them exactly, and applying their
 // inverses afterwards restores the caller's state bit for bit.
 std::mutex g_tune_mu;
@@ -174,12 +176,12 @@ int autotune_fused_k(rcs_ctx *c, const std::vector<HostGate> &hg, int *k_out) {
             fwd.U[size_t(j) * d + (j + 1) % d] = cd(0.0, 1.0);  // i * cyclic shift
             inv.U[size_t((j + 1) % d) * d + j] = cd(0.0, -1.0);
         }
-        int rc = launch_pass_simt(c->psi, c->n, fwd, c->stream);  // warm-up
-        if (rc == RCS_OK) rc = launch_pass_simt(c->psi, c->n, inv, c->stream);
+        int rc = launch_pass_simt(c->psi, c->n, fwd, nullptr, c->stream);  // warm-up
+        if (rc == RCS_OK) rc = launch_pass_simt(c->psi, c->n, inv, nullptr, c->stream);
         cudaEventRecord(e0, c->stream);
-        for (int r = 0; r < reps && rc == RCS_OK; ++r) rc = launch_pass_simt(c->psi, c->n, fwd, c->stream);
+        for (int r = 0; r < reps && rc == RCS_OK; ++r) rc = launch_pass_simt(c->psi, c->n, fwd, nullptr, c->stream);
         cudaEventRecord(e1, c->stream);
-        for (int r = 0; r < reps && rc == RCS_OK; ++r) rc = launch_pass_simt(c->psi, c->n, inv, c->stream);
+        for (int r = 0; r < reps && rc == RCS_OK; ++r) rc = launch_pass_simt(c->psi, c->n, inv, nullptr, c->stream);
         if (rc != RCS_OK) {
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
@@ -244,7 +246,7 @@ int build_plan(rcs_ctx *ctx, int n, const std::vector<HostGate> &hg, const rcs_o
             break;
         case RCS_PREC_FP32_FUSED: {
             int k = o.k_max > 0 ? o.k_max : 4;
-            if (k < 2 || k > 5) return fail(ctx, RCS_ERR_ARG, "FP32_FUSED k_max must be 2..5");
+            if (k < 2 || k > kSimtKMax) return fail(ctx, RCS_ERR_ARG, "FP32_FUSED k_max must be 2..7");
             plan->k_max = std::min(k, n);
             if (n == 1) plan_plain(n, hg, &plan->passes);
             else fused(plan->k_max, 0);
@@ -322,7 +324,9 @@ int restore_layout(rcs_ctx *c) {
 
 bool plan_tf32(const Plan &plan) { return plan.precision == RCS_PREC_TF32X3; }
 
-// Builds the split operand images of every tensor-core pass into one host buffer.
+// Builds the device images of a plan into one host buffer: the split operand images of
+// every tensor-core pass, the pair kernel's images, and the FP32 U of every SIMT pass
+// wider than the kernel parameters hold.
 void build_ops_images(Plan &plan, std::vector<uint8_t> *img) {
     const bool tf32 = plan_tf32(plan);
     const size_t per = tc_ops_bytes(tf32);
@@ -339,10 +343,18 @@ void build_ops_images(Plan &plan, std::vector<uint8_t> *img) {
                 plan.pair_offset[i] = int64_t(total);
                 total += pair_ops_bytes();
             }
+    // FP32 images of the wide SIMT passes (16-byte multiples, so every offset stays aligned)
+    for (size_t i = 0; i < plan.passes.size(); ++i)
+        if (plan.passes[i].kind == PASS_SIMT && simt_ops_bytes(plan.passes[i].k) > 0) {
+            plan.tc_offset[i] = int64_t(total);
+            total += simt_ops_bytes(plan.passes[i].k);
+        }
     img->assign(total, 0);
     // independent images in disjoint slices of the buffer
     host_parallel_for(plan.passes.size(), [&](size_t i) {
-        if (plan.tc_offset[i] >= 0) tc_build_ops(plan.passes[i], img->data() + plan.tc_offset[i], tf32);
+        if (plan.tc_offset[i] >= 0 && plan.passes[i].kind == PASS_SIMT)
+            simt_build_ops(plan.passes[i], img->data() + plan.tc_offset[i]);
+        else if (plan.tc_offset[i] >= 0) tc_build_ops(plan.passes[i], img->data() + plan.tc_offset[i], tf32);
         if (plan.pair_offset[i] >= 0) pair_build_ops(plan.passes[i], img->data() + plan.pair_offset[i]);
     });
 }
@@ -358,16 +370,6 @@ Pass compact_pass(const Pass &p, uint64_t T) {
     Pass q = p;
     for (int i = 0; i < p.k; ++i) q.t[i] = std::popcount(T & ((1ull << p.t[i]) - 1ull));
     return q;
-}
-
-int launch_one(rcs_ctx *c, float2 *psi, int n, const Pass &p, const uint8_t *ops, bool tf32) {
-    switch (p.kind) {
-        case PASS_1Q:
-        case PASS_2Q: return launch_pass_plain(psi, n, p, c->stream);
-        case PASS_SIMT: return launch_pass_simt(psi, n, p, c->stream);
-        case PASS_TC: return launch_pass_tc(psi, n, p, ops, c->d_err, c->stream, tf32);
-        default: return RCS_ERR_ARG;
-    }
 }
 
 // Launches the plan's passes. from_zero: the state is |0...0> (it may not be written
@@ -455,7 +457,7 @@ int launch_plan_pass(void *psi, int n, const Pass &p, const uint8_t *ops, int *d
     switch (p.kind) {
         case PASS_1Q:
         case PASS_2Q: return launch_pass_plain(psi, n, p, stream);
-        case PASS_SIMT: return launch_pass_simt(psi, n, p, stream);
+        case PASS_SIMT: return launch_pass_simt(psi, n, p, ops, stream);
         case PASS_TC: return launch_pass_tc(psi, n, p, ops, d_err, stream, tf32);
         default: return RCS_ERR_ARG;
     }
@@ -526,7 +528,9 @@ int launch_pass_range(const Plan &plan, void *psi, int n, size_t first, size_t e
             i += 2;
             continue;
         }
-        const uint8_t *ops = p.kind == PASS_TC ? d_ops + plan.tc_offset[i] : nullptr;
+        const uint8_t *ops = plan.tc_offset.size() == plan.passes.size() && plan.tc_offset[i] >= 0
+                                 ? d_ops + plan.tc_offset[i]
+                                 : nullptr;
         if (launch_plan_pass(psi, n, p, ops, d_err, stream, tf32) != RCS_OK) return RCS_ERR_CUDA;
         ++*launches;
         ++i;
@@ -734,7 +738,7 @@ namespace {
 // One caller unitary as a pass on the context's stored qubits: validated (targets,
 // unitarity to 1e-6), reordered to ascending targets, and given the kernel kind.
 int unitary_pass(rcs_ctx *c, int k, const int32_t *targets, const double *u_re_im, Pass *out) {
-    if (k < 1 || k > kTcK || !targets || !u_re_im) return fail(c, RCS_ERR_ARG, "k must be 1..6 with targets and u");
+    if (k < 1 || k > kSimtKMax || !targets || !u_re_im) return fail(c, RCS_ERR_ARG, "k must be 1..7 with targets and u");
     if (k > c->n) return fail(c, RCS_ERR_QUBIT, "more targets than qubits");
     uint64_t seen = 0;
     for (int i = 0; i < k; ++i) {
@@ -773,9 +777,7 @@ int unitary_pass(rcs_ctx *c, int k, const int32_t *targets, const double *u_re_i
     for (int j = 0; j < d; ++j)
         for (int l = 0; l < d; ++l) p.U[size_t(remap(j)) * d + remap(l)] = U[size_t(j) * d + l];
     const bool tc_prec = c->opts.precision == RCS_PREC_BF16X3 || c->opts.precision == RCS_PREC_TF32X3;
-    if (k == kTcK && tc_prec && c->n >= kTcK + 7) p.kind = PASS_TC;
-    else if (k <= 5) p.kind = PASS_SIMT;
-    else return fail(c, RCS_ERR_UNSUPPORTED, "6-qubit unitaries need a tensor-core precision and n >= 13");
+    p.kind = k == kTcK && tc_prec && c->n >= kTcK + 7 ? PASS_TC : PASS_SIMT;
     return RCS_OK;
 }
 }  // namespace
@@ -816,7 +818,7 @@ int rcs_apply_unitaries(rcs_ctx *c, size_t count, const int32_t *k, const int32_
     plan.passes.resize(count);
     size_t off = 0;
     for (size_t i = 0; i < count; ++i) {
-        if (k[i] < 1 || k[i] > kTcK) return fail(c, RCS_ERR_ARG, "k must be 1..6 with targets and u");
+        if (k[i] < 1 || k[i] > kSimtKMax) return fail(c, RCS_ERR_ARG, "k must be 1..7 with targets and u");
         if (int rc = unitary_pass(c, k[i], targets + off, u_re_im[i], &plan.passes[i]); rc != RCS_OK) return rc;
         off += size_t(k[i]);
     }

@@ -16,6 +16,8 @@ using cd = std::complex<double>;
 constexpr int kMaxQubits = 34;
 constexpr int kSampleBlockLog2 = 10;  // sampler block = 1024 amplitudes
 constexpr int kTcK = 6;               // width of the tensor-core fused pass
+constexpr int kSimtParamK = 5;        // widest FP32 fused pass with U in the kernel parameters
+constexpr int kSimtKMax = 7;          // widest FP32 fused pass (U from a device image above 5)
 
 // Records msg as the calling thread's last error (rcs_last_error(NULL)); returns code.
 int set_thread_error(int code, const std::string &msg);
@@ -65,7 +67,8 @@ struct Plan {
     // device copies, per context device (uploaded lazily)
     int dev = -1;
     void *d_tc_ops = nullptr;   // hi/lo operand images of PASS_TC passes
-    std::vector<int64_t> tc_offset;  // byte offset of each pass's image (-1 if none)
+    std::vector<int64_t> tc_offset;  // byte offset of each pass's image (-1 if none): the split
+                                     // images of PASS_TC passes, the FP32 U of wide PASS_SIMT ones
     std::vector<int64_t> pair_offset;  // byte offset of each pass's pair-kernel image (-1 if none)
 };
 
@@ -139,7 +142,13 @@ int run_substages(const Plan &plan, const std::vector<SubStage> &stages, void *p
 // Launches one pass of a plan on a 2^n-amplitude state (ops: its operand image, if any).
 int launch_plan_pass(void *psi, int n, const Pass &p, const uint8_t *ops, int *d_err, void *stream, bool tf32);
 int launch_pass_plain(void *psi, int n, const Pass &p, void *stream);
-int launch_pass_simt(void *psi, int n, const Pass &p, void *stream);
+// Fused FP32 SIMT pass of width p.k = 1..kSimtKMax. Widths up to kSimtParamK carry U in
+// the kernel parameters (ops unused); wider ones read it from ops, the device copy of
+// simt_build_ops(p) (16-byte aligned), and give RCS_ERR_ARG without it.
+int launch_pass_simt(void *psi, int n, const Pass &p, const uint8_t *ops, void *stream);
+// Bytes of a SIMT pass's device image (0 for widths up to kSimtParamK) and its builder.
+size_t simt_ops_bytes(int k);
+void simt_build_ops(const Pass &p, uint8_t *out);
 // Sets the fused SIMT kernels' shared-memory attribute on the current device (once);
 // launch_pass_simt calls it, and a caller about to capture a graph calls it first.
 int simt_prepare_device();

@@ -13,6 +13,9 @@
 //    unitary travels in the kernel's parameter space (constant bank) and the
 //    fully unrolled complex mat-vec reads it as immediate constant operands.
 //    8 * 2^K real flop per amplitude: HBM-bound up to K = 4 on GB300.
+//  * k_fused_wide<K>: fused K = 6 or 7 qubit unitaries, a CTA per tile of 64
+//    slices, U from a device image in shared memory (see below). Bound by the
+//    FP32 FMA pipe.
 #include "dev_common.cuh"
 #include "internal.h"
 
@@ -230,6 +233,116 @@ __global__ void __launch_bounds__(256, simt_blocks_per_sm<K>()) k_fused_simt(flo
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
+// ---- k_fused_wide<K>: fused 6- and 7-qubit unitaries on FP32 SIMT cores.
+//
+// A 2^K x 2^K complex matrix no longer fits the parameter space or a thread's registers,
+// so a CTA applies it to a tile of kWideT consecutive slices as a small complex GEMM in
+// shared memory: out[s][j] = sum_l U[j][l] in[s][l], FP32 fused multiply-adds over l in
+// increasing order. U comes from a device image laid out [l][j] (float2 re, im) and is
+// copied into shared memory once per CTA. Each tile is copied in with cp.async into a
+// [j][s] buffer (rows padded by one amplitude), multiplied, written back into the same
+// buffer and stored with the same coalesced [j][s] walk. 8 * 2^K real flop per amplitude
+// (32 and 64 flop/B): far past the FP32 ridge, so these passes are bound by the FMA pipe.
+constexpr int kWideT = 64;        // slices per tile
+constexpr int kWideThreads = 256;  // 16 slice groups x 16 output groups
+constexpr int kWideRow = kWideT + 1;
+
+template <int K>
+constexpr size_t wide_smem_bytes() {
+    return size_t(1 << K) * (1 << K) * 8 + size_t(1 << K) * kWideRow * 8 + size_t(1 << K) * 8;
+}
+
+struct WideArgs {
+    int t[8];  // ascending targets (K used)
+    uint64_t slices;
+};
+
+template <int K>
+__global__ void __launch_bounds__(kWideThreads, K == 6 ? 3 : 1)
+    k_fused_wide(float2 *__restrict__ psi, const float2 *__restrict__ ut, const __grid_constant__ WideArgs a) {
+    constexpr int D = 1 << K;
+    constexpr int RJ = D / 16;  // outputs per thread
+    extern __shared__ __align__(16) unsigned char wide_smem[];
+    float2 *U = reinterpret_cast<float2 *>(wide_smem);  // [l][j]
+    float2 *buf = U + D * D;                             // [j][kWideRow]
+    uint64_t *offs = reinterpret_cast<uint64_t *>(buf + D * kWideRow);
+    const int tid = threadIdx.x;
+    const uint64_t slices = a.slices;
+    for (int j = tid; j < D; j += kWideThreads) {
+        uint64_t o = 0;
+#pragma unroll
+        for (int i = 0; i < K; ++i)
+            if ((j >> i) & 1) o |= 1ull << a.t[i];
+        offs[j] = o;
+    }
+    {  // U image: D * D * 8 bytes in 16-byte copies
+        const uint32_t dst0 = uint32_t(__cvta_generic_to_shared(U));
+        for (int c = tid; c < D * D / 2; c += kWideThreads)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst0 + uint32_t(c) * 16u), "l"(ut + 2 * c)
+                         : "memory");
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    __syncthreads();  // offs
+    const uint64_t ntiles = (slices + kWideT - 1) / kWideT;
+    // copy / store walk: slice s = tid % 64, rows j = tid / 64 + 4 i
+    const int ws = tid & (kWideT - 1), wj = tid / kWideT;
+    // compute: slices sg + 16 r, outputs jg + 16 c
+    const int jg = tid & 15, sg = tid >> 4;
+    const uint32_t buf0 = uint32_t(__cvta_generic_to_shared(buf));
+#pragma unroll 1
+    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint64_t s = tile * kWideT + uint64_t(ws);
+        const bool live = s < slices;
+        uint64_t base = s;
+#pragma unroll
+        for (int i = 0; i < K; ++i) base = insert_zero(base, a.t[i]);
+        if (live) {
+#pragma unroll 4
+            for (int j = wj; j < D; j += kWideThreads / kWideT) {
+                const uint32_t dst = buf0 + uint32_t(j * kWideRow + ws) * 8u;
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(psi + (base | offs[j])) : "memory");
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();
+        float2 acc[4][RJ];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < RJ; ++c) acc[r][c] = make_float2(0.f, 0.f);
+#pragma unroll 2
+        for (int l = 0; l < D; ++l) {
+            float2 x[4], u[RJ];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) x[r] = buf[l * kWideRow + sg + 16 * r];
+#pragma unroll
+            for (int c = 0; c < RJ; ++c) u[c] = U[l * D + jg + 16 * c];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < RJ; ++c) {
+                    acc[r][c].x = fmaf(u[c].x, x[r].x, acc[r][c].x);
+                    acc[r][c].x = fmaf(-u[c].y, x[r].y, acc[r][c].x);
+                    acc[r][c].y = fmaf(u[c].x, x[r].y, acc[r][c].y);
+                    acc[r][c].y = fmaf(u[c].y, x[r].x, acc[r][c].y);
+                }
+        }
+        __syncthreads();  // every input read before the buffer takes the outputs
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < RJ; ++c) buf[(jg + 16 * c) * kWideRow + sg + 16 * r] = acc[r][c];
+        __syncthreads();
+        if (live) {
+#pragma unroll 4
+            for (int j = wj; j < D; j += kWideThreads / kWideT) psi[base | offs[j]] = buf[j * kWideRow + ws];
+        }
+        __syncthreads();  // the stores have read the buffer before the next tile's copies
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 __global__ void k_init_zero(float4 *__restrict__ psi4, uint64_t n4) {
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n4; i += stride)
@@ -335,13 +448,43 @@ static int simt_attr() {
     return RCS_OK;
 }
 
+// Shared-memory attribute of k_fused_wide<K> on the current device (once).
+template <int K>
+static int wide_attr() {
+    static bool attr_done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && attr_done[dev]) return RCS_OK;
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_fused_wide<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(wide_smem_bytes<K>()));
+    if (e != cudaSuccess) return note_launch_error("wide fused kernel shared-memory attribute", e);
+    if (dev >= 0 && dev < 64) attr_done[dev] = true;
+    return RCS_OK;
+}
+
 int simt_prepare_device() {
     int rc = simt_attr<1>();
     if (rc == RCS_OK) rc = simt_attr<2>();
     if (rc == RCS_OK) rc = simt_attr<3>();
     if (rc == RCS_OK) rc = simt_attr<4>();
     if (rc == RCS_OK) rc = simt_attr<5>();
+    if (rc == RCS_OK) rc = wide_attr<6>();
+    if (rc == RCS_OK) rc = wide_attr<7>();
     return rc;
+}
+
+size_t simt_ops_bytes(int k) { return k > kSimtParamK ? size_t(8) << (2 * k) : 0; }
+
+// FP32 image of a wide pass: entry (l, j) = U[j][l] as (re, im), l-major.
+void simt_build_ops(const Pass &p, uint8_t *out) {
+    const int D = 1 << p.k;
+    auto *f = reinterpret_cast<float *>(out);
+    for (int l = 0; l < D; ++l)
+        for (int j = 0; j < D; ++j) {
+            const cd &u = p.U[size_t(j) * D + l];
+            f[2 * (size_t(l) * D + j)] = float(u.real());
+            f[2 * (size_t(l) * D + j) + 1] = float(u.imag());
+        }
 }
 
 template <int K>
@@ -364,7 +507,21 @@ static int launch_simt_k(float2 *psi, int n, const Pass &p, cudaStream_t st) {
     return check_launch();
 }
 
-int launch_pass_simt(void *psi, int n, const Pass &p, void *stream) {
+template <int K>
+static int launch_wide_k(float2 *psi, int n, const Pass &p, const uint8_t *ops, cudaStream_t st) {
+    if (!ops || (reinterpret_cast<uintptr_t>(ops) & 15u)) return RCS_ERR_ARG;
+    WideArgs a{};
+    for (int i = 0; i < K; ++i) a.t[i] = p.t[i];
+    a.slices = 1ull << (n - K);
+    if (int rc = wide_attr<K>(); rc != RCS_OK) return rc;
+    const uint64_t tiles = (a.slices + kWideT - 1) / kWideT;
+    const uint64_t resident = uint64_t(device_sm_count()) * (K == 6 ? 3 : 1);
+    const unsigned grid = unsigned(tiles < resident ? tiles : resident);
+    k_fused_wide<K><<<grid, kWideThreads, wide_smem_bytes<K>(), st>>>(psi, reinterpret_cast<const float2 *>(ops), a);
+    return check_launch();
+}
+
+int launch_pass_simt(void *psi, int n, const Pass &p, const uint8_t *ops, void *stream) {
     auto st = static_cast<cudaStream_t>(stream);
     auto *s = static_cast<float2 *>(psi);
     if (p.k > n) return RCS_ERR_ARG;
@@ -374,6 +531,8 @@ int launch_pass_simt(void *psi, int n, const Pass &p, void *stream) {
         case 3: return launch_simt_k<3>(s, n, p, st);
         case 4: return launch_simt_k<4>(s, n, p, st);
         case 5: return launch_simt_k<5>(s, n, p, st);
+        case 6: return launch_wide_k<6>(s, n, p, ops, st);
+        case 7: return launch_wide_k<7>(s, n, p, ops, st);
         default: return RCS_ERR_UNSUPPORTED;
     }
 }

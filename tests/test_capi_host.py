@@ -50,6 +50,12 @@ def test_error_messages_without_gpu(lib):
         capi.rcs_plan_build(4, np.array([C.make_gate(9, 0)]))
     with pytest.raises(capi.RcsError):
         capi.rcs_plan_build(40, np.zeros(0, dtype=C.GATE_DTYPE))
+    # FP32 fused widths are 2..7
+    gates = C.generate(C.grid_for_n(10), cycles=2, pattern="EFGH", seed=1).gates
+    for k in (1, 8):
+        with pytest.raises(capi.RcsError) as e:
+            capi.rcs_plan_build(10, gates, capi.RCS_PREC_FP32_FUSED, k)
+        assert e.value.code == capi.RCS_ERR_ARG and "2..7" in str(e.value)
 
 
 def _plan_passes(plan):
@@ -60,7 +66,8 @@ def _plan_passes(plan):
 @pytest.mark.parametrize("precision,kmax,n", [(capi.RCS_PREC_FP32_FUSED, 2, 10), (capi.RCS_PREC_FP32_FUSED, 4, 10),
                                               (capi.RCS_PREC_FP32_FUSED, 5, 9), (capi.RCS_PREC_BF16X3, 0, 13),
                                               (capi.RCS_PREC_FP32_FUSED, 4, 14), (capi.RCS_PREC_FP32_PLAIN, 0, 9),
-                                              (capi.RCS_PREC_TF32X3, 0, 14), (capi.RCS_PREC_BF16X3, 0, 20)])
+                                              (capi.RCS_PREC_TF32X3, 0, 14), (capi.RCS_PREC_BF16X3, 0, 20),
+                                              (capi.RCS_PREC_FP32_FUSED, 6, 12), (capi.RCS_PREC_FP32_FUSED, 7, 13)])
 def test_fused_plan_reproduces_circuit(oracle, lib, precision, kmax, n):
     """Applying the planned passes (FP64 matrices) with the oracle equals applying
     the circuit gate by gate with the oracle."""

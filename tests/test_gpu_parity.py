@@ -120,7 +120,7 @@ def test_circuit_20q_vs_oracle(lib, oracle, circ20, precision):
         capi.rcs_destroy(ctx)
 
 
-@pytest.mark.parametrize("k_max", [2, 3, 5])
+@pytest.mark.parametrize("k_max", [2, 3, 5, 6, 7])
 def test_fused_widths_vs_oracle(lib, oracle, circ20, k_max):
     circ, want = circ20
     ctx = run_gpu(circ.grid, circ.gates, capi.RCS_PREC_FP32_FUSED, k_max)
@@ -233,6 +233,50 @@ def _fixed_k_state(n, circ, psi0, k):
 # targets with four or more below qubit 5 run the memory-order (staged) kernel variant,
 # the others the slice-order variant, whose stores depend on the lowest target (bit 0,
 # bit 1 and higher each take another path); n >= 22 gives every CTA several tiles
+# One FP32 pass of width k (6 or 7: U in shared memory): each real output sums 2 * 2^k
+# FP32 products of U (rounded to FP32, 2^-24 relative) and the FP32 state by fused
+# multiply-adds, so |error| <= (2 * 2^k + 1) 2^-24 * sum |U_jl| |x_l|
+# <= (2 * 2^k + 1) 2^-24 * |slice|_2 (a row of U has unit norm).
+@pytest.mark.parametrize("precision", [capi.RCS_PREC_FP32_FUSED, capi.RCS_PREC_BF16X3])
+@pytest.mark.parametrize("n,targets", [(6, [0, 1, 2, 3, 4, 5]), (7, [6, 0, 5, 1, 4, 2, 3]), (8, [1, 2, 3, 5, 6, 7]),
+                                       (10, [9, 0, 4, 7, 2, 5, 8]), (13, [0, 1, 2, 3, 4, 5]),
+                                       (13, [6, 7, 8, 9, 10, 11, 12]), (16, [2, 5, 1, 15, 8, 11]),
+                                       (17, [3, 16, 9, 0, 12, 6, 14]), (20, [5, 6, 7, 8, 9, 10, 11])])
+def test_wide_simt_pass_vs_oracle(lib, oracle, n, targets, precision):
+    """6- and 7-qubit unitaries on the FP32 SIMT kernel (from 6 to 20 qubits, so from one
+    ragged tile of 1 slice to 2^14 slices), element by element against the oracle. On a
+    BF16X3 context a 7-qubit unitary, and a 6-qubit one below 13 qubits, take the same
+    FP32 kernel."""
+    if precision == capi.RCS_PREC_BF16X3 and len(targets) == 6 and n >= 13:
+        pytest.skip("the tensor-core kernel takes this case (test_tc_pass_vs_oracle)")
+    k = len(targets)
+    rng = np.random.default_rng(n * 1000 + k * 10 + targets[0])
+    psi0 = (rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)).astype(np.complex64)
+    psi0 /= np.linalg.norm(psi0)
+    ctx = capi.rcs_create(n, precision)
+    try:
+        capi.rcs_state_write(ctx, psi0)
+        want = psi0.astype(np.complex128)
+        for rep in range(2):
+            U = rand_unitary(1 << k, rng)
+            capi.rcs_apply_unitary(ctx, targets, U)
+            capi.rcs_sync(ctx)
+            got = capi.rcs_state_read(ctx).astype(np.complex128)
+            prev = want.copy()
+            oracle.apply_matrix(want, targets, U)
+            mask = sum(1 << t for t in targets)
+            base = np.arange(1 << n) & ~mask
+            slice_norm2 = np.zeros(1 << n)
+            np.add.at(slice_norm2, base, np.abs(prev) ** 2)
+            bound = (2 * 2**k + 1) * 2.0**-24 * math.sqrt(slice_norm2.max())
+            err = np.abs(got - want).max()
+            assert err <= bound, (rep, err, bound)
+            assert infidelity(got, want) <= 1e-10
+            want = got
+    finally:
+        capi.rcs_destroy(ctx)
+
+
 TC_PASS_BOUND = {capi.RCS_PREC_BF16X3: (4e-5, 1e-8), capi.RCS_PREC_TF32X3: (4e-6, 1e-10)}
 
 
