@@ -410,7 +410,7 @@ def config_measure(args, torch, capi, name: str):
             for k in amps if k != "fp32_fused_k4"}
         out["speedup_bf16x3_vs_fp32_plain"] = out["fp32_plain"]["apply_s"] / out["bf16x3"]["apply_s"]
         if n <= 30 and n >= 20:
-            out["fp32_wide_pass"] = wide_pass_measure(torch, capi, ctx, n, stream)
+            out["fp32_wide_pass"] = wide_pass_measure(torch, capi, n, stream)
     finally:
         capi.rcs_destroy(ctx)
     if not args.no_cpu:
@@ -424,13 +424,15 @@ def config_measure(args, torch, capi, name: str):
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 
-def wide_pass_measure(torch, capi, ctx, n, stream):
-    """One full-state FP32 pass of width 6 and of width 7 (U in shared memory), three
+def wide_pass_measure(torch, capi, n, stream):
+    """One full-state pass of each FP32 fused width 4..7 on its own FP32 context (width 4
+    carries U in the kernel parameters, 5..7 multiply tiles by U in shared memory), three
     timed launches each after one untimed, against the FP32 FMA peak: 8 * 2^k real flop
-    per amplitude."""
+    per amplitude, and against HBM: 16 bytes per amplitude."""
     rng = np.random.default_rng(7)
     res = {}
-    for k in (6, 7):
+    ctx = capi.rcs_create(n, capi.RCS_PREC_FP32_FUSED, stream=stream.cuda_stream)
+    for k in (4, 5, 6, 7):
         targets = list(range(5, 5 + k))  # above the 32 slices a warp stores side by side
         mats = []
         for _ in range(4):
@@ -449,6 +451,7 @@ def wide_pass_measure(torch, capi, ctx, n, stream):
         res[f"k{k}"] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12,
                         "alu_frac": flops / (ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
                         "hbm_frac": 16.0 * 2**n / (ms / 1e3) / 1e9 / measured_peaks()["hbm_gbs"]}
+    capi.rcs_destroy(ctx)
     res["peak_tflops"] = FP32_PEAK_TFLOPS
     res["peak_source"] = "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (unit counts and maximum clock)"
     return res

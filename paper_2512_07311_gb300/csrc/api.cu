@@ -176,12 +176,29 @@ int autotune_fused_k(rcs_ctx *c, const std::vector<HostGate> &hg, int *k_out) {
             fwd.U[size_t(j) * d + (j + 1) % d] = cd(0.0, 1.0);  // i * cyclic shift
             inv.U[size_t((j + 1) % d) * d + j] = cd(0.0, -1.0);
         }
-        int rc = launch_pass_simt(c->psi, c->n, fwd, nullptr, c->stream);  // warm-up
-        if (rc == RCS_OK) rc = launch_pass_simt(c->psi, c->n, inv, nullptr, c->stream);
+        // widths above the parameter-space kernel read U from a device image
+        const size_t ib = simt_ops_bytes(k);
+        uint8_t *d_img = nullptr;
+        int rc = RCS_OK;
+        if (ib > 0) {
+            std::vector<uint8_t> img(2 * ib);
+            simt_build_ops(fwd, img.data());
+            simt_build_ops(inv, img.data() + ib);
+            if (cudaMalloc(&d_img, 2 * ib) != cudaSuccess ||
+                cudaMemcpy(d_img, img.data(), 2 * ib, cudaMemcpyHostToDevice) != cudaSuccess)
+                rc = RCS_ERR_CUDA;
+        }
+        const uint8_t *ops_f = d_img, *ops_i = d_img ? d_img + ib : nullptr;
+        if (rc == RCS_OK) rc = launch_pass_simt(c->psi, c->n, fwd, ops_f, c->stream);  // warm-up
+        if (rc == RCS_OK) rc = launch_pass_simt(c->psi, c->n, inv, ops_i, c->stream);
         cudaEventRecord(e0, c->stream);
-        for (int r = 0; r < reps && rc == RCS_OK; ++r) rc = launch_pass_simt(c->psi, c->n, fwd, nullptr, c->stream);
+        for (int r = 0; r < reps && rc == RCS_OK; ++r) rc = launch_pass_simt(c->psi, c->n, fwd, ops_f, c->stream);
         cudaEventRecord(e1, c->stream);
-        for (int r = 0; r < reps && rc == RCS_OK; ++r) rc = launch_pass_simt(c->psi, c->n, inv, nullptr, c->stream);
+        for (int r = 0; r < reps && rc == RCS_OK; ++r) rc = launch_pass_simt(c->psi, c->n, inv, ops_i, c->stream);
+        if (d_img) {
+            cudaStreamSynchronize(c->stream);
+            cudaFree(d_img);
+        }
         if (rc != RCS_OK) {
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);

@@ -16,8 +16,8 @@ using cd = std::complex<double>;
 constexpr int kMaxQubits = 34;
 constexpr int kSampleBlockLog2 = 10;  // sampler block = 1024 amplitudes
 constexpr int kTcK = 6;               // width of the tensor-core fused pass
-constexpr int kSimtParamK = 5;        // widest FP32 fused pass with U in the kernel parameters
-constexpr int kSimtKMax = 7;          // widest FP32 fused pass (U from a device image above 5)
+constexpr int kSimtParamK = 4;        // widest FP32 fused pass with U in the kernel parameters
+constexpr int kSimtKMax = 7;          // widest FP32 fused pass (U from a device image above 4)
 
 // Records msg as the calling thread's last error (rcs_last_error(NULL)); returns code.
 int set_thread_error(int code, const std::string &msg);

@@ -6,14 +6,14 @@
 //    target at qubit 0 the pair itself is one float4. HBM-bound: 16 * 2^n bytes
 //    per gate against 8 (1q) or 16 (2q) real flop per amplitude, i.e. 0.5 or 1
 //    flop per byte, far below the FP32 ridge.
-//  * k_fused_simt<K>: one launch per fused K-qubit unitary (K <= 5). Thread =
+//  * k_fused_simt<K>: one launch per fused K-qubit unitary (K <= 4). Thread =
 //    one slice of 2^K amplitudes (the amplitudes that differ only in the target
 //    bits); lanes of a warp take consecutive slices, so each load instruction
 //    covers consecutive addresses along the lowest non-target qubits. The
 //    unitary travels in the kernel's parameter space (constant bank) and the
 //    fully unrolled complex mat-vec reads it as immediate constant operands.
 //    8 * 2^K real flop per amplitude: HBM-bound up to K = 4 on GB300.
-//  * k_fused_wide<K>: fused K = 6 or 7 qubit unitaries, a CTA per tile of 64
+//  * k_fused_wide<K>: fused K = 5, 6 or 7 qubit unitaries, a CTA per tile of 64
 //    slices, U from a device image in shared memory (see below). Bound by the
 //    FP32 FMA pipe.
 #include "dev_common.cuh"
@@ -159,7 +159,7 @@ struct SimtArgs {
 // spilling (the two stages of 256 slices x 2^K amplitudes fit in shared memory).
 template <int K>
 constexpr int simt_blocks_per_sm() {
-    return K >= 5 ? 1 : (K == 4 ? 2 : 3);
+    return K == 4 ? 2 : 3;
 }
 
 // One thread per 2^K-amplitude slice, persistent over the slices (grid-stride). Each
@@ -233,23 +233,47 @@ __global__ void __launch_bounds__(256, simt_blocks_per_sm<K>()) k_fused_simt(flo
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// ---- k_fused_wide<K>: fused 6- and 7-qubit unitaries on FP32 SIMT cores.
+// ---- k_fused_wide<K>: fused 5- to 7-qubit unitaries on FP32 SIMT cores.
 //
-// A 2^K x 2^K complex matrix no longer fits the parameter space or a thread's registers,
-// so a CTA applies it to a tile of kWideT consecutive slices as a small complex GEMM in
-// shared memory: out[s][j] = sum_l U[j][l] in[s][l], FP32 fused multiply-adds over l in
-// increasing order. U comes from a device image laid out [l][j] (float2 re, im) and is
+// From K = 5 a 2^K x 2^K complex matrix no longer fits the constant cache (as packed
+// operands it is 16 KB at K = 5), and from K = 6 not the parameter space or a thread's
+// registers, so a CTA applies it to a tile of T consecutive slices as a small complex
+// GEMM in shared memory: out[s][j] = sum_l U[j][l] in[s][l], FP32 fused multiply-adds
+// over l in increasing order. U comes from a device image laid out [l][j] (float2 re, im) and is
 // copied into shared memory once per CTA. Each tile is copied in with cp.async into a
 // [j][s] buffer (rows padded by one amplitude), multiplied, written back into the same
 // buffer and stored with the same coalesced [j][s] walk. 8 * 2^K real flop per amplitude
-// (32 and 64 flop/B): far past the FP32 ridge, so these passes are bound by the FMA pipe.
-constexpr int kWideT = 64;        // slices per tile
-constexpr int kWideThreads = 256;  // 16 slice groups x 16 output groups
-constexpr int kWideRow = kWideT + 1;
+// (16 to 64 flop/B): past the FP32 ridge, so these passes are bound by the FMA pipe.
+constexpr int kWideThreads = 256;
+
+// Per width: each thread computes RS slices x RJ outputs (slices sg + SG r, outputs
+// jg + JG c; JG x SG = 256 threads), so a tile holds T = SG x RS slices. K = 5 takes
+// 8 x 4 (256 slices, 12 shared loads per 128 multiply-adds); K = 6 and 7 take 4 x 4 and
+// 4 x 8 on 64 slices, as far as U and the tile fit in shared memory. Resident CTAs per
+// SM: by the registers at K = 5 (74 KB each), by shared memory at K = 6 (65 KB) and
+// K = 7 (194 KB).
+template <int K>
+struct WideShape {
+    static constexpr int D = 1 << K;
+    static constexpr int RS = K == 5 ? 8 : 4;
+    static constexpr int RJ = K == 7 ? 8 : 4;
+    static constexpr int JG = D / RJ;
+    static constexpr int SG = kWideThreads / JG;
+    static constexpr int T = SG * RS;
+    static constexpr int Row = T + 1;  // buffer row, padded by one amplitude
+    static constexpr int Blocks = K == 5 ? 2 : (K == 6 ? 3 : 1);
+    static constexpr size_t Smem = size_t(D) * D * 8 + size_t(D) * Row * 8 + size_t(D) * 8;
+    static_assert(JG * SG == kWideThreads && T <= kWideThreads && kWideThreads % T == 0, "tile shape");
+};
+
+template <int K>
+constexpr int wide_blocks_per_sm() {
+    return WideShape<K>::Blocks;
+}
 
 template <int K>
 constexpr size_t wide_smem_bytes() {
-    return size_t(1 << K) * (1 << K) * 8 + size_t(1 << K) * kWideRow * 8 + size_t(1 << K) * 8;
+    return WideShape<K>::Smem;
 }
 
 struct WideArgs {
@@ -258,14 +282,14 @@ struct WideArgs {
 };
 
 template <int K>
-__global__ void __launch_bounds__(kWideThreads, K == 6 ? 3 : 1)
+__global__ void __launch_bounds__(kWideThreads, wide_blocks_per_sm<K>())
     k_fused_wide(float2 *__restrict__ psi, const float2 *__restrict__ ut, const __grid_constant__ WideArgs a) {
-    constexpr int D = 1 << K;
-    constexpr int RJ = D / 16;  // outputs per thread
+    using S = WideShape<K>;
+    constexpr int D = S::D, RS = S::RS, RJ = S::RJ, JG = S::JG, SG = S::SG, T = S::T, Row = S::Row;
     extern __shared__ __align__(16) unsigned char wide_smem[];
     float2 *U = reinterpret_cast<float2 *>(wide_smem);  // [l][j]
-    float2 *buf = U + D * D;                             // [j][kWideRow]
-    uint64_t *offs = reinterpret_cast<uint64_t *>(buf + D * kWideRow);
+    float2 *buf = U + D * D;                             // [j][Row]
+    uint64_t *offs = reinterpret_cast<uint64_t *>(buf + D * Row);
     const int tid = threadIdx.x;
     const uint64_t slices = a.slices;
     for (int j = tid; j < D; j += kWideThreads) {
@@ -283,43 +307,43 @@ __global__ void __launch_bounds__(kWideThreads, K == 6 ? 3 : 1)
         asm volatile("cp.async.commit_group;" ::: "memory");
     }
     __syncthreads();  // offs
-    const uint64_t ntiles = (slices + kWideT - 1) / kWideT;
-    // copy / store walk: slice s = tid % 64, rows j = tid / 64 + 4 i
-    const int ws = tid & (kWideT - 1), wj = tid / kWideT;
-    // compute: slices sg + 16 r, outputs jg + 16 c
-    const int jg = tid & 15, sg = tid >> 4;
+    const uint64_t ntiles = (slices + T - 1) / T;
+    // copy / store walk: slice s = tid % T, rows j = tid / T + (256 / T) i
+    const int ws = tid % T, wj = tid / T;
+    // compute: slices sg + SG r, outputs jg + JG c
+    const int jg = tid % JG, sg = tid / JG;
     const uint32_t buf0 = uint32_t(__cvta_generic_to_shared(buf));
 #pragma unroll 1
     for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const uint64_t s = tile * kWideT + uint64_t(ws);
+        const uint64_t s = tile * T + uint64_t(ws);
         const bool live = s < slices;
         uint64_t base = s;
 #pragma unroll
         for (int i = 0; i < K; ++i) base = insert_zero(base, a.t[i]);
         if (live) {
 #pragma unroll 4
-            for (int j = wj; j < D; j += kWideThreads / kWideT) {
-                const uint32_t dst = buf0 + uint32_t(j * kWideRow + ws) * 8u;
+            for (int j = wj; j < D; j += kWideThreads / T) {
+                const uint32_t dst = buf0 + uint32_t(j * Row + ws) * 8u;
                 asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(psi + (base | offs[j])) : "memory");
             }
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
         asm volatile("cp.async.wait_all;" ::: "memory");
         __syncthreads();
-        float2 acc[4][RJ];
+        float2 acc[RS][RJ];
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < RS; ++r)
 #pragma unroll
             for (int c = 0; c < RJ; ++c) acc[r][c] = make_float2(0.f, 0.f);
 #pragma unroll 2
         for (int l = 0; l < D; ++l) {
-            float2 x[4], u[RJ];
+            float2 x[RS], u[RJ];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) x[r] = buf[l * kWideRow + sg + 16 * r];
+            for (int r = 0; r < RS; ++r) x[r] = buf[l * Row + sg + SG * r];
 #pragma unroll
-            for (int c = 0; c < RJ; ++c) u[c] = U[l * D + jg + 16 * c];
+            for (int c = 0; c < RJ; ++c) u[c] = U[l * D + jg + JG * c];
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+            for (int r = 0; r < RS; ++r)
 #pragma unroll
                 for (int c = 0; c < RJ; ++c) {
                     acc[r][c].x = fmaf(u[c].x, x[r].x, acc[r][c].x);
@@ -330,13 +354,13 @@ __global__ void __launch_bounds__(kWideThreads, K == 6 ? 3 : 1)
         }
         __syncthreads();  // every input read before the buffer takes the outputs
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < RS; ++r)
 #pragma unroll
-            for (int c = 0; c < RJ; ++c) buf[(jg + 16 * c) * kWideRow + sg + 16 * r] = acc[r][c];
+            for (int c = 0; c < RJ; ++c) buf[(jg + JG * c) * Row + sg + SG * r] = acc[r][c];
         __syncthreads();
         if (live) {
 #pragma unroll 4
-            for (int j = wj; j < D; j += kWideThreads / kWideT) psi[base | offs[j]] = buf[j * kWideRow + ws];
+            for (int j = wj; j < D; j += kWideThreads / T) psi[base | offs[j]] = buf[j * Row + ws];
         }
         __syncthreads();  // the stores have read the buffer before the next tile's copies
     }
@@ -467,7 +491,7 @@ int simt_prepare_device() {
     if (rc == RCS_OK) rc = simt_attr<2>();
     if (rc == RCS_OK) rc = simt_attr<3>();
     if (rc == RCS_OK) rc = simt_attr<4>();
-    if (rc == RCS_OK) rc = simt_attr<5>();
+    if (rc == RCS_OK) rc = wide_attr<5>();
     if (rc == RCS_OK) rc = wide_attr<6>();
     if (rc == RCS_OK) rc = wide_attr<7>();
     return rc;
@@ -514,8 +538,8 @@ static int launch_wide_k(float2 *psi, int n, const Pass &p, const uint8_t *ops, 
     for (int i = 0; i < K; ++i) a.t[i] = p.t[i];
     a.slices = 1ull << (n - K);
     if (int rc = wide_attr<K>(); rc != RCS_OK) return rc;
-    const uint64_t tiles = (a.slices + kWideT - 1) / kWideT;
-    const uint64_t resident = uint64_t(device_sm_count()) * (K == 6 ? 3 : 1);
+    const uint64_t tiles = (a.slices + WideShape<K>::T - 1) / WideShape<K>::T;
+    const uint64_t resident = uint64_t(device_sm_count()) * wide_blocks_per_sm<K>();
     const unsigned grid = unsigned(tiles < resident ? tiles : resident);
     k_fused_wide<K><<<grid, kWideThreads, wide_smem_bytes<K>(), st>>>(psi, reinterpret_cast<const float2 *>(ops), a);
     return check_launch();
@@ -530,7 +554,7 @@ int launch_pass_simt(void *psi, int n, const Pass &p, const uint8_t *ops, void *
         case 2: return launch_simt_k<2>(s, n, p, st);
         case 3: return launch_simt_k<3>(s, n, p, st);
         case 4: return launch_simt_k<4>(s, n, p, st);
-        case 5: return launch_simt_k<5>(s, n, p, st);
+        case 5: return launch_wide_k<5>(s, n, p, ops, st);
         case 6: return launch_wide_k<6>(s, n, p, ops, st);
         case 7: return launch_wide_k<7>(s, n, p, ops, st);
         default: return RCS_ERR_UNSUPPORTED;

@@ -233,20 +233,21 @@ def _fixed_k_state(n, circ, psi0, k):
 # targets with four or more below qubit 5 run the memory-order (staged) kernel variant,
 # the others the slice-order variant, whose stores depend on the lowest target (bit 0,
 # bit 1 and higher each take another path); n >= 22 gives every CTA several tiles
-# One FP32 pass of width k (6 or 7: U in shared memory): each real output sums 2 * 2^k
+# One FP32 pass of width k (5, 6 or 7: U in shared memory): each real output sums 2 * 2^k
 # FP32 products of U (rounded to FP32, 2^-24 relative) and the FP32 state by fused
 # multiply-adds, so |error| <= (2 * 2^k + 1) 2^-24 * sum |U_jl| |x_l|
 # <= (2 * 2^k + 1) 2^-24 * |slice|_2 (a row of U has unit norm).
 @pytest.mark.parametrize("precision", [capi.RCS_PREC_FP32_FUSED, capi.RCS_PREC_BF16X3])
-@pytest.mark.parametrize("n,targets", [(6, [0, 1, 2, 3, 4, 5]), (7, [6, 0, 5, 1, 4, 2, 3]), (8, [1, 2, 3, 5, 6, 7]),
+@pytest.mark.parametrize("n,targets", [(5, [4, 3, 2, 1, 0]), (9, [0, 2, 4, 6, 8]), (21, [1, 2, 3, 4, 20]),
+                                       (6, [0, 1, 2, 3, 4, 5]), (7, [6, 0, 5, 1, 4, 2, 3]), (8, [1, 2, 3, 5, 6, 7]),
                                        (10, [9, 0, 4, 7, 2, 5, 8]), (13, [0, 1, 2, 3, 4, 5]),
                                        (13, [6, 7, 8, 9, 10, 11, 12]), (16, [2, 5, 1, 15, 8, 11]),
                                        (17, [3, 16, 9, 0, 12, 6, 14]), (20, [5, 6, 7, 8, 9, 10, 11])])
 def test_wide_simt_pass_vs_oracle(lib, oracle, n, targets, precision):
-    """6- and 7-qubit unitaries on the FP32 SIMT kernel (from 6 to 20 qubits, so from one
-    ragged tile of 1 slice to 2^14 slices), element by element against the oracle. On a
-    BF16X3 context a 7-qubit unitary, and a 6-qubit one below 13 qubits, take the same
-    FP32 kernel."""
+    """5- to 7-qubit unitaries on the tiled FP32 SIMT kernel (from 5 to 21 qubits, so from
+    one ragged tile of 1 slice to 2^16 slices), element by element against the oracle. On a
+    BF16X3 context a 5- or 7-qubit unitary, and a 6-qubit one below 13 qubits, take the
+    same FP32 kernel."""
     if precision == capi.RCS_PREC_BF16X3 and len(targets) == 6 and n >= 13:
         pytest.skip("the tensor-core kernel takes this case (test_tc_pass_vs_oracle)")
     k = len(targets)
