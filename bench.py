@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--pair-passes", action="store_true",
                     help="time the opt-in two-unitary kernel (RCS_OPT_PAIR_PASSES) as the headline path")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--fp32-wide-pass", type=int, default=0, metavar="N",
+                    help="only time one full-state pass of each fused FP32 width 4..7 on an N-qubit state "
+                         "(20..30) and print it as one JSON line")
     ap.add_argument("--oracle-check", action="store_true",
                     help="also build the workload's whole state with the CPU oracle (timed: apply, sample, XEB) and "
                          "compare every GPU path with it at full size; needs host memory for the complex128 state "
@@ -518,6 +521,12 @@ def main():
     capi.load()
     if args.workload == "batch64":
         return run_batch(args, torch, capi)
+    if args.fp32_wide_pass:
+        if not 20 <= args.fp32_wide_pass <= 30:
+            raise SystemExit("--fp32-wide-pass takes 20..30 qubits")
+        res = wide_pass_measure(torch, capi, args.fp32_wide_pass, torch.cuda.current_stream())
+        print(json.dumps({"fp32_wide_pass": res, "qubits": args.fp32_wide_pass}))
+        return 0
     cfg = C.CONFIGS[args.workload]
     if args.qubits:
         circ = C.generate(C.grid_for_n(args.qubits), 20, "ABCDCDAB", seed=2)
