@@ -88,8 +88,8 @@ typedef struct {
 } rcs_gate;
 
 /* Options. precision: RCS_PREC_*. k_max: largest fused block (FP32_FUSED: 2..7,
- * default 4; widths 6 and 7 multiply each tile of 64 slices by U in shared memory and
- * are bound by the FP32 FMA pipe, at 32 and 64 flop per byte; BF16X3 and TF32X3: 6).
+ * default 4; widths 5 to 7 multiply tiles of slices by U in shared memory and are
+ * bound by the FP32 FMA pipe, at 16 to 64 flop per byte; BF16X3 and TF32X3: 6).
  * autotune: 1 = for FP32_FUSED, rcs_apply_circuit chooses
  * k_max in 2..5 minimising (passes at width k) x (measured time of a width-k pass
  * on this state), by timed trial passes on the first call for this qubit count on

@@ -16,7 +16,8 @@ from paper_2512_07311_gb300 import circuits as C
 pytestmark = pytest.mark.gpu
 
 PATHS = [("fp32_plain", capi.RCS_PREC_FP32_PLAIN, 0), ("fp32_fused_k4", capi.RCS_PREC_FP32_FUSED, 4),
-         ("fp32_fused_k5", capi.RCS_PREC_FP32_FUSED, 5), ("bf16x3_tensor_core", capi.RCS_PREC_BF16X3, 0),
+         ("fp32_fused_k5", capi.RCS_PREC_FP32_FUSED, 5), ("fp32_fused_k6", capi.RCS_PREC_FP32_FUSED, 6),
+         ("fp32_fused_k7", capi.RCS_PREC_FP32_FUSED, 7), ("bf16x3_tensor_core", capi.RCS_PREC_BF16X3, 0),
          ("tf32x3_tensor_core", capi.RCS_PREC_TF32X3, 0)]
 
 
