@@ -247,22 +247,24 @@ __global__ void __launch_bounds__(256, simt_blocks_per_sm<K>()) k_fused_simt(flo
 constexpr int kWideThreads = 256;
 
 // Per width: each thread computes RS slices x RJ outputs (slices sg + SG r, outputs
-// jg + JG c; JG x SG = 256 threads), so a tile holds T = SG x RS slices. K = 5 takes
-// 8 x 4 (256 slices, 12 shared loads per 128 multiply-adds); K = 6 and 7 take 4 x 4 and
-// 4 x 8 on 64 slices, as far as U and the tile fit in shared memory. Resident CTAs per
-// SM: by the registers at K = 5 (74 KB each), by shared memory at K = 6 (65 KB) and
-// K = 7 (194 KB).
+// jg + JG c; JG x SG = 256 threads), so a tile holds T = SG x RS slices: 4 x 4 on 128
+// slices at K = 5, 4 x 4 and 4 x 8 on 64 slices at K = 6 and 7. Up to K = 6 two tile
+// buffers let the next tile's copies run under the current tile's multiply-adds (the
+// CTAs of an SM otherwise stay in step: all copying, then all multiplying); at K = 7 only
+// one fits beside U. Resident CTAs per SM, by shared memory: three at K = 5 (74 KB), two
+// at K = 6 (99 KB), one at K = 7 (194 KB).
 template <int K>
 struct WideShape {
     static constexpr int D = 1 << K;
-    static constexpr int RS = K == 5 ? 8 : 4;
+    static constexpr int RS = 4;
     static constexpr int RJ = K == 7 ? 8 : 4;
     static constexpr int JG = D / RJ;
     static constexpr int SG = kWideThreads / JG;
     static constexpr int T = SG * RS;
     static constexpr int Row = T + 1;  // buffer row, padded by one amplitude
-    static constexpr int Blocks = K == 5 ? 2 : (K == 6 ? 3 : 1);
-    static constexpr size_t Smem = size_t(D) * D * 8 + size_t(D) * Row * 8 + size_t(D) * 8;
+    static constexpr bool Dbl = K <= 6;  // two tile buffers: the next tile's copies run under the multiply-adds
+    static constexpr int Blocks = K == 5 ? 3 : (K == 6 ? 2 : 1);
+    static constexpr size_t Smem = size_t(D) * D * 8 + (Dbl ? 2 : 1) * size_t(D) * Row * 8 + size_t(D) * 8;
     static_assert(JG * SG == kWideThreads && T <= kWideThreads && kWideThreads % T == 0, "tile shape");
 };
 
@@ -288,8 +290,8 @@ __global__ void __launch_bounds__(kWideThreads, wide_blocks_per_sm<K>())
     constexpr int D = S::D, RS = S::RS, RJ = S::RJ, JG = S::JG, SG = S::SG, T = S::T, Row = S::Row;
     extern __shared__ __align__(16) unsigned char wide_smem[];
     float2 *U = reinterpret_cast<float2 *>(wide_smem);  // [l][j]
-    float2 *buf = U + D * D;                             // [j][Row]
-    uint64_t *offs = reinterpret_cast<uint64_t *>(buf + D * Row);
+    float2 *buf = U + D * D;                             // [j][Row], twice when double-buffered
+    uint64_t *offs = reinterpret_cast<uint64_t *>(buf + (S::Dbl ? 2 : 1) * D * Row);
     const int tid = threadIdx.x;
     const uint64_t slices = a.slices;
     for (int j = tid; j < D; j += kWideThreads) {
@@ -313,22 +315,41 @@ __global__ void __launch_bounds__(kWideThreads, wide_blocks_per_sm<K>())
     // compute: slices sg + SG r, outputs jg + JG c
     const int jg = tid % JG, sg = tid / JG;
     const uint32_t buf0 = uint32_t(__cvta_generic_to_shared(buf));
+    auto base_of = [&](uint64_t sl) {
+        uint64_t b = sl;
+#pragma unroll
+        for (int i = 0; i < K; ++i) b = insert_zero(b, a.t[i]);
+        return b;
+    };
+    // copies of tile `tile` into buffer `which` (one commit group per call, possibly empty)
+    auto issue = [&](uint64_t tile, int which) {
+        const uint64_t sl = tile * T + uint64_t(ws);
+        if (tile < ntiles && sl < slices) {
+            const uint64_t b = base_of(sl);
+            const uint32_t dst0 = buf0 + uint32_t(which * D * Row) * 8u;
+#pragma unroll 4
+            for (int j = wj; j < D; j += kWideThreads / T) {
+                const uint32_t dst = dst0 + uint32_t(j * Row + ws) * 8u;
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(psi + (b | offs[j])) : "memory");
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    int cur = 0;
+    if (S::Dbl) issue(blockIdx.x, 0);
 #pragma unroll 1
     for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const uint64_t s = tile * T + uint64_t(ws);
         const bool live = s < slices;
-        uint64_t base = s;
-#pragma unroll
-        for (int i = 0; i < K; ++i) base = insert_zero(base, a.t[i]);
-        if (live) {
-#pragma unroll 4
-            for (int j = wj; j < D; j += kWideThreads / T) {
-                const uint32_t dst = buf0 + uint32_t(j * Row + ws) * 8u;
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(psi + (base | offs[j])) : "memory");
-            }
+        const uint64_t base = base_of(s);
+        if (S::Dbl) {
+            issue(tile + gridDim.x, cur ^ 1);  // that buffer's last stores ended before the last barrier
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            issue(tile, 0);
+            asm volatile("cp.async.wait_all;" ::: "memory");
         }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_all;" ::: "memory");
+        float2 *bt = buf + cur * D * Row;
         __syncthreads();
         float2 acc[RS][RJ];
 #pragma unroll
@@ -339,7 +360,7 @@ __global__ void __launch_bounds__(kWideThreads, wide_blocks_per_sm<K>())
         for (int l = 0; l < D; ++l) {
             float2 x[RS], u[RJ];
 #pragma unroll
-            for (int r = 0; r < RS; ++r) x[r] = buf[l * Row + sg + SG * r];
+            for (int r = 0; r < RS; ++r) x[r] = bt[l * Row + sg + SG * r];
 #pragma unroll
             for (int c = 0; c < RJ; ++c) u[c] = U[l * D + jg + JG * c];
 #pragma unroll
@@ -356,13 +377,14 @@ __global__ void __launch_bounds__(kWideThreads, wide_blocks_per_sm<K>())
 #pragma unroll
         for (int r = 0; r < RS; ++r)
 #pragma unroll
-            for (int c = 0; c < RJ; ++c) buf[(jg + JG * c) * Row + sg + SG * r] = acc[r][c];
+            for (int c = 0; c < RJ; ++c) bt[(jg + JG * c) * Row + sg + SG * r] = acc[r][c];
         __syncthreads();
         if (live) {
 #pragma unroll 4
-            for (int j = wj; j < D; j += kWideThreads / T) psi[base | offs[j]] = buf[j * Row + ws];
+            for (int j = wj; j < D; j += kWideThreads / T) psi[base | offs[j]] = bt[j * Row + ws];
         }
-        __syncthreads();  // the stores have read the buffer before the next tile's copies
+        __syncthreads();  // the stores have read the buffer before copies into it are issued
+        if (S::Dbl) cur ^= 1;
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
