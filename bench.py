@@ -429,9 +429,11 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 def wide_pass_measure(torch, capi, n, stream):
     """One full-state pass of each FP32 fused width 4..7 on its own FP32 context (width 4
-    carries U in the kernel parameters, 5..7 multiply tiles by U in shared memory), three
-    timed launches each after one untimed, against the FP32 FMA peak: 8 * 2^k real flop
-    per amplitude, and against HBM: 16 bytes per amplitude."""
+    carries U in the kernel parameters, 5..7 multiply tiles by U in shared memory): one
+    untimed pass, then three passes applied in one call and timed by the library's CUDA
+    events around their launches (rcs_last_pass_timing; the host's validation and upload of
+    the matrices fall outside). Against the FP32 FMA peak (8 * 2^k real flop per amplitude)
+    and against HBM (16 bytes per amplitude)."""
     rng = np.random.default_rng(7)
     res = {}
     ctx = capi.rcs_create(n, capi.RCS_PREC_FP32_FUSED, stream=stream.cuda_stream)
@@ -443,13 +445,9 @@ def wide_pass_measure(torch, capi, n, stream):
             q, r = np.linalg.qr(a)
             mats.append(q * (np.diag(r) / abs(np.diag(r))))
         capi.rcs_apply_unitary(ctx, targets, mats[0])
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        ev[0].record(stream)
-        for u in mats[1:]:
-            capi.rcs_apply_unitary(ctx, targets, u)
-        ev[1].record(stream)
-        stream.synchronize()
-        ms = ev[0].elapsed_time(ev[1]) / 3
+        capi.rcs_apply_unitaries(ctx, [(targets, u) for u in mats[1:]])
+        total_ms, launches = capi.rcs_last_pass_timing(ctx)
+        ms = total_ms / launches
         flops = 8.0 * 2**k * 2**n
         res[f"k{k}"] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12,
                         "alu_frac": flops / (ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
