@@ -445,6 +445,11 @@ int note_launch_error(const char *what, cudaError_t e) {
     return RCS_ERR_CUDA;
 }
 
+int note_launch_refusal(int code, const char *msg) {
+    g_launch_err = msg;
+    return code;
+}
+
 int launch_status(const char *what) {
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? RCS_OK : note_launch_error(what, e);

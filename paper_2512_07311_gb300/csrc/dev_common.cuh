@@ -69,6 +69,8 @@ int device_sm_count();
 // Launch bookkeeping: the launchers return RCS_ERR_CUDA on failure and leave the
 // CUDA error text for the caller (consumed with take_launch_error()).
 int note_launch_error(const char *what, cudaError_t e);
+// Records msg as the launch error text (for a launch refused before it reached CUDA); returns code.
+int note_launch_refusal(int code, const char *msg);
 int launch_status(const char *what);  // RCS_OK, or notes cudaGetLastError()
 
 }  // namespace rcs

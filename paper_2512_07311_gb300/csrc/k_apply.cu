@@ -13,9 +13,9 @@
 //    unitary travels in the kernel's parameter space (constant bank) and the
 //    fully unrolled complex mat-vec reads it as immediate constant operands.
 //    8 * 2^K real flop per amplitude: HBM-bound up to K = 4 on GB300.
-//  * k_fused_wide<K>: fused K = 5, 6 or 7 qubit unitaries, a CTA per tile of 64
-//    slices, U from a device image in shared memory (see below). Bound by the
-//    FP32 FMA pipe.
+//  * k_fused_wide<K>: fused K = 5, 6 or 7 qubit unitaries, a CTA per tile of 128
+//    (K = 5) or 64 slices, U from a device image in shared memory (see below).
+//    Bound by the FP32 FMA pipe.
 #include "dev_common.cuh"
 #include "internal.h"
 
@@ -555,7 +555,8 @@ static int launch_simt_k(float2 *psi, int n, const Pass &p, cudaStream_t st) {
 
 template <int K>
 static int launch_wide_k(float2 *psi, int n, const Pass &p, const uint8_t *ops, cudaStream_t st) {
-    if (!ops || (reinterpret_cast<uintptr_t>(ops) & 15u)) return RCS_ERR_ARG;
+    if (!ops || (reinterpret_cast<uintptr_t>(ops) & 15u))
+        return note_launch_refusal(RCS_ERR_ARG, "fused pass of width 5..7 without a 16-byte aligned U image");
     WideArgs a{};
     for (int i = 0; i < K; ++i) a.t[i] = p.t[i];
     a.slices = 1ull << (n - K);
