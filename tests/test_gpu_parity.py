@@ -450,6 +450,13 @@ def test_amplitudes_and_errors(lib):
         with pytest.raises(capi.RcsError) as e:
             capi.rcs_apply_circuit(ctx, np.array([C.make_gate(C.SQRT_X, n)]))
         assert e.value.code == capi.RCS_ERR_QUBIT
+        # dense unitaries take 1..7 targets; a list with a bad entry is rejected before any runs
+        with pytest.raises(capi.RcsError) as e:
+            capi.rcs_apply_unitary(ctx, list(range(8)), np.eye(256))
+        assert e.value.code == capi.RCS_ERR_ARG and "1..7" in str(e.value)
+        with pytest.raises(capi.RcsError) as e:
+            capi.rcs_apply_unitaries(ctx, [(list(range(7)), np.eye(128)), (list(range(8)), np.eye(256))])
+        assert e.value.code == capi.RCS_ERR_ARG
         # the state is unchanged by the rejected calls
         np.testing.assert_array_equal(capi.rcs_state_read(ctx), full)
     finally:
