@@ -1,6 +1,8 @@
 // Gate-fusion planner: merges runs of 1- and 2-qubit gates into dense k-qubit
 // unitaries (one state pass each). The paper's engine is closed and describes no
-// fusion; this is a greedy frontier construction on the gate DAG.
+// fusion; this is a search over frontier constructions on the gate DAG: greedy
+// growth, beam searches over grown blocks, and a beam search over closures of
+// connected qubit sets.
 //
 // A block is grown from the current frontier (gates whose predecessors on every
 // one of their qubits are already placed), adding frontier gates while the block
@@ -18,6 +20,8 @@
 #include <functional>
 #include <condition_variable>
 #include <atomic>
+#include <map>
+#include <set>
 #include <unordered_set>
 #include <thread>
 
@@ -422,12 +426,207 @@ std::vector<Block> beam_blocking(const Dag &d, size_t G, int k_max, int window, 
     }
 }
 
+// Beam search whose moves are closures. From a frontier, the closure of a qubit set T is
+// every unplaced gate that can run before any gate touching a qubit outside T: the gates
+// whose support -- the qubits of the gate and of all its unplaced ancestors -- lies in T.
+// One scan in circuit order gives every support, so a candidate set's closure size is the
+// number of gates whose support it contains. The candidate sets are the connected
+// k_max-qubit sets of the circuit's coupling graph inside `allow`, plus the block grown
+// from every ready seed (as in beam_blocking, so that qubits without couplings progress
+// too). Each step keeps the `expand` largest moves per state and the `width` states with
+// the most gates placed, merging equal frontiers. The first state with `target` gates
+// placed ends the search. Returns false (no blocking) when there are more than max_sets
+// candidate sets, as on densely coupled circuits. Ties go to the lower set, then the
+// earlier state, so the result does not depend on thread timing.
+bool closure_beam(const Dag &d, size_t G, int k_max, int width, int expand, const std::vector<size_t> &head0,
+                  size_t placed0, uint64_t allow, size_t target, std::vector<Block> *result,
+                  size_t max_sets = 20000) {
+    result->clear();
+    const int n = d.n;
+    std::vector<uint64_t> adj(size_t(n), 0);
+    for (size_t g = 0; g < G; ++g)
+        if (std::popcount(d.mask[g]) == 2) {
+            const int a = std::countr_zero(d.mask[g]);
+            const int b = 63 - std::countl_zero(d.mask[g]);
+            adj[size_t(a)] |= 1ull << b;
+            adj[size_t(b)] |= 1ull << a;
+        }
+    std::vector<uint64_t> sets;
+    {
+        std::unordered_set<uint64_t> cur;
+        for (int q = 0; q < n; ++q)
+            if ((allow >> q) & 1) cur.insert(1ull << q);
+        for (int s = 1; s < k_max; ++s) {
+            std::unordered_set<uint64_t> nx;
+            for (uint64_t m : cur) {
+                uint64_t nb = 0;
+                for (uint64_t r = m; r; r &= r - 1) nb |= adj[size_t(std::countr_zero(r))];
+                nb &= ~m & allow;
+                for (; nb; nb &= nb - 1) nx.insert(m | (1ull << std::countr_zero(nb)));
+            }
+            if (nx.size() > max_sets) return false;
+            if (nx.empty()) break;
+            cur = std::move(nx);
+        }
+        sets.assign(cur.begin(), cur.end());
+        std::sort(sets.begin(), sets.end());
+    }
+    std::vector<std::vector<uint32_t>> sets_with;  // the candidate sets holding qubit q
+    sets_with.resize(size_t(n));
+    for (size_t i = 0; i < sets.size(); ++i)
+        for (uint64_t r = sets[i]; r; r &= r - 1) sets_with[size_t(std::countr_zero(r))].push_back(uint32_t(i));
+
+    // Supports of the unplaced gates under `head` that fit a candidate set, merged by value
+    // as (support, gates). Supports only widen along a qubit's gates, so the scan stops once
+    // every qubit's latest support is too wide or its gates are done.
+    auto supports = [&](const std::vector<size_t> &head, std::vector<std::pair<uint64_t, uint32_t>> *out) {
+        uint64_t last[64] = {};
+        size_t rem[64] = {};
+        uint64_t live = 0;
+        size_t first = G;
+        for (int q = 0; q < n; ++q) {
+            rem[q] = d.queue[size_t(q)].size() - head[size_t(q)];
+            if (rem[q] && ((allow >> q) & 1)) live |= 1ull << q;
+            if (rem[q]) first = std::min(first, size_t(d.queue[size_t(q)][head[size_t(q)]]));
+        }
+        out->clear();
+        for (size_t gi = first; gi < G && live; ++gi) {
+            if (d.placed(gi, head)) continue;
+            const uint64_t m = d.mask[gi];
+            uint64_t s = m;
+            for (uint64_t r = m; r; r &= r - 1) s |= last[std::countr_zero(r)];
+            for (uint64_t r = m; r; r &= r - 1) {
+                const int q = std::countr_zero(r);
+                last[q] = s;
+                if (--rem[q] == 0) live &= ~(1ull << q);
+            }
+            if (std::popcount(s) <= k_max && (s & ~allow) == 0) out->emplace_back(s, 1u);
+            else live &= ~m;
+        }
+        std::sort(out->begin(), out->end());
+        size_t w = 0;
+        for (size_t i = 0; i < out->size(); ++i) {
+            if (w > 0 && (*out)[w - 1].first == (*out)[i].first) (*out)[w - 1].second += (*out)[i].second;
+            else (*out)[w++] = (*out)[i];
+        }
+        out->resize(w);
+    };
+    // Takes the closure of T as a block (circuit order is an application order).
+    auto take_closure = [&](std::vector<size_t> &head, uint64_t T, Block *b) {
+        uint64_t last[64] = {};
+        std::vector<int> in;
+        size_t first = G;
+        for (int q = 0; q < n; ++q)
+            if (head[size_t(q)] < d.queue[size_t(q)].size())
+                first = std::min(first, size_t(d.queue[size_t(q)][head[size_t(q)]]));
+        for (size_t gi = first; gi < G; ++gi) {
+            if (d.placed(gi, head)) continue;
+            const uint64_t m = d.mask[gi];
+            uint64_t s = m;
+            for (uint64_t r = m; r; r &= r - 1) s |= last[std::countr_zero(r)];
+            for (uint64_t r = m; r; r &= r - 1) last[std::countr_zero(r)] = s;
+            if ((s & ~T) == 0) in.push_back(int(gi));
+        }
+        for (int gi : in) {
+            d.take(gi, head);
+            b->gates.push_back(gi);
+            b->Q |= d.mask[size_t(gi)];
+        }
+    };
+
+    struct Node {
+        int parent;
+        std::vector<int> gates;
+    };
+    struct State {
+        std::vector<size_t> head;
+        size_t placed;
+        int node;
+    };
+    struct Move {
+        size_t placed;
+        uint64_t T;  // closure of T, or (seed >= 0) the block grown from seed
+        int seed;
+    };
+    std::vector<std::vector<Node>> steps;
+    std::vector<State> states{State{head0, placed0, -1}};
+    while (true) {
+        for (const State &st : states)
+            if (st.placed >= target) {
+                result->resize(steps.size());
+                int node = st.node;
+                for (size_t k = steps.size(); k-- > 0;) {
+                    (*result)[k].gates = steps[k][size_t(node)].gates;
+                    node = steps[k][size_t(node)].parent;
+                }
+                return true;
+            }
+        std::vector<std::vector<Move>> slot(states.size());
+        parallel_for(states.size(), [&](size_t i) {
+            std::vector<std::pair<uint64_t, uint32_t>> sup;
+            supports(states[i].head, &sup);
+            std::vector<uint32_t> cnt(sets.size(), 0);
+            for (const auto &s : sup)
+                for (uint32_t si : sets_with[size_t(std::countr_zero(s.first))])
+                    if ((s.first & ~sets[si]) == 0) cnt[si] += s.second;
+            std::vector<Move> ms;
+            for (size_t si = 0; si < sets.size(); ++si)
+                if (cnt[si]) ms.push_back(Move{states[i].placed + cnt[si], sets[si], -1});
+            std::vector<int> seeds;
+            d.ready_gates(states[i].head, &seeds);
+            for (int sd : seeds) {
+                if (d.mask[size_t(sd)] & ~allow) continue;
+                std::vector<size_t> h = states[i].head;
+                const Block b = grow(d, h, k_max, 0, sd, allow);
+                ms.push_back(Move{states[i].placed + b.gates.size(), 0, sd});
+            }
+            // the `expand` largest, earlier moves first on ties
+            const size_t keep = std::min(ms.size(), size_t(expand));
+            std::vector<uint32_t> idx(ms.size());
+            for (size_t j = 0; j < idx.size(); ++j) idx[j] = uint32_t(j);
+            std::partial_sort(idx.begin(), idx.begin() + std::ptrdiff_t(keep), idx.end(), [&](uint32_t x, uint32_t y) {
+                return ms[x].placed != ms[y].placed ? ms[x].placed > ms[y].placed : x < y;
+            });
+            slot[i].clear();
+            for (size_t j = 0; j < keep; ++j) slot[i].push_back(ms[idx[j]]);
+        });
+        std::vector<std::pair<size_t, size_t>> order;
+        for (size_t i = 0; i < slot.size(); ++i)
+            for (size_t j = 0; j < slot[i].size(); ++j) order.emplace_back(i, j);
+        std::stable_sort(order.begin(), order.end(), [&](const auto &x, const auto &y) {
+            return slot[x.first][x.second].placed > slot[y.first][y.second].placed;
+        });
+        std::set<std::vector<size_t>> seen;
+        std::vector<Node> nodes;
+        std::vector<State> next;
+        for (const auto &o : order) {
+            if (int(next.size()) >= width) break;
+            const Move &mv = slot[o.first][o.second];
+            std::vector<size_t> h = states[o.first].head;
+            Block b;
+            if (mv.seed >= 0) b = grow(d, h, k_max, 0, mv.seed, allow);
+            else take_closure(h, mv.T, &b);
+            if (!seen.insert(h).second) continue;
+            nodes.push_back(Node{states[o.first].node, std::move(b.gates)});
+            next.push_back(State{std::move(h), mv.placed, int(nodes.size() - 1)});
+        }
+        if (next.empty()) return false;
+        steps.push_back(std::move(nodes));
+        states = std::move(next);
+    }
+}
+
 }  // namespace
 
 constexpr int kBeamWidth = 32;  // states kept per step of the beam search
 constexpr int kBeamExpand = 8;  // blocks grown per state and step
 constexpr int kSmallBeamWidth = 8;  // the beam that ranks the staged candidates
 constexpr int kSmallBeamExpand = 4;
+constexpr int kClosureWidth = 16;       // states kept per step of the closure search
+constexpr int kClosureExpand = 16;      // moves kept per state and step
+constexpr int kStageClosureWidth = 8;   // the closure search inside a sub-state stage
+constexpr int kStageClosureExpand = 8;
+constexpr int kFinalists = 3;           // staged candidates whose rest gets the full searches
 
 namespace {
 
@@ -487,15 +686,19 @@ double zero_cost(const Dag &d, const std::vector<Block> &b, int n, int span) {
 
 // Fuses the gates into blocks of at most k_max qubits. Several greedy blockings are
 // built -- the plain frontier rule, best-seed growth with affinity windows of 0, 1, 2,
-// 3 and 6 next gates, and a beam search -- and the one with the fewest blocks is kept.
+// 3 and 6 next gates, two beam searches over grown blocks and a beam search over
+// closures of connected qubit sets -- and the one with the fewest blocks is kept.
 // For a run from |0...0> (from_zero) the choice is by cost instead (full passes plus
-// sub-state passes x 2^(width - n)), and staged candidates are added. For a single
-// stage of k = 2..5 excluded qubits, or two nested stages (k1 then k2 < k1 excluded),
-// the excluded qubits are chosen greedily to keep the largest closure (the gates that
-// precede every gate on them). Each stage's closure is blocked inside its sub-state,
-// and the rest of the circuit after it (by a small beam search to pick the candidate,
-// then by the full one). On the 34-qubit 20-cycle workload at k = 6 this takes the full-state passes
-// from 37 (45 passes, 8 of them on a 30-qubit sub-state) to 27.
+// sub-state passes x 2^(width - n)), and staged candidates are added: one to three
+// nested stages, each leaving k qubits out of its sub-state (a subset of those the
+// stage before it left out). The excluded qubits are chosen greedily to keep the
+// largest closure (the gates that precede every gate on them). Each stage's closure is
+// blocked inside its sub-state (greedy growth or the closure search, whichever needs
+// fewer blocks; stages shared by several candidates are blocked once), and the rest of
+// the circuit after it is estimated by a small beam search. The best few candidates by
+// that estimate get the full searches for their rest. On the 34-qubit 20-cycle
+// workload at k = 6 this takes the full-state passes from 37 (45 passes, 8 of them on
+// a 30-qubit sub-state) to 26, after 17 passes on sub-states of 28, 30 and 32 qubits.
 Blocking plan_blocks(int n, const std::vector<HostGate> &gates, int k_max, bool from_zero) {
     const size_t G = gates.size();
     k_max = std::max(2, std::min(k_max, n));
@@ -517,16 +720,6 @@ Blocking plan_blocks(int n, const std::vector<HostGate> &gates, int k_max, bool 
     const int default_span = n - 4;
     const uint64_t full = n >= 64 ? ~0ull : ((1ull << n) - 1ull);
     // staged candidates: k excluded qubits per stage, nested and shrinking
-    struct Cand {
-        double est = 1e300;  // greedy rest + sub-state cost
-        double sub_cost = 0.0;
-        std::vector<int> ks;
-        std::vector<uint64_t> X;
-        std::vector<int> stage_end;
-        std::vector<Block> pre;
-        std::vector<size_t> head;
-        size_t placed = 0;
-    };
     std::vector<std::vector<int>> configs;
     if (from_zero && G > 0) {
         const int min_sub = std::max(kTcK + 7, k_max);
@@ -535,45 +728,83 @@ Blocking plan_blocks(int n, const std::vector<HostGate> &gates, int k_max, bool 
         const int pairs[][2] = {{4, 2}, {5, 2}, {6, 2}, {4, 3}, {5, 3}, {6, 3}, {7, 3}, {6, 4}, {7, 4}};
         for (const auto &pr : pairs)
             if (n - pr[0] >= min_sub) configs.push_back({pr[0], pr[1]});
+        const int triples[][3] = {{6, 4, 2}, {7, 4, 2}, {8, 4, 2}, {5, 3, 2}, {6, 3, 2}, {7, 5, 2}, {8, 5, 2}};
+        for (const auto &tr : triples)
+            if (n - tr[0] >= min_sub) configs.push_back({tr[0], tr[1], tr[2]});
     }
+    // Every distinct stage prefix of the candidates, parents before children: the stage's
+    // excluded qubits, its blocks, the frontier after it and the sub-state cost so far.
+    struct Stage {
+        std::vector<int> ks;
+        int parent = -1;
+        uint64_t X = 0;
+        std::vector<Block> blocks;
+        std::vector<size_t> head;
+        size_t placed = 0;
+        double cost = 0.0;
+    };
+    std::vector<Stage> stages;
+    std::map<std::vector<int>, int> stage_of;
+    auto block_stage = [&](Stage &s) {
+        const Stage *par = s.parent >= 0 ? &stages[size_t(s.parent)] : nullptr;
+        const int k = s.ks.back();
+        const std::vector<size_t> head0 = par ? par->head : std::vector<size_t>(size_t(n), 0);
+        const size_t placed0 = par ? par->placed : 0;
+        s.X = choose_excluded(d, head0, k, par ? par->X : full, full);
+        const uint64_t allow = full & ~s.X;
+        s.head = head0;
+        s.placed = placed0;
+        s.blocks = blocking_from(d, G, k_max, 2, true, allow, s.head, s.placed);
+        // both searches place the same gates (the stage's closure), so the frontier is the same
+        std::vector<Block> cl;
+        if (closure_beam(d, G, k_max, kStageClosureWidth, kStageClosureExpand, head0, placed0, allow, s.placed, &cl) &&
+            cl.size() < s.blocks.size())
+            s.blocks = std::move(cl);
+        s.cost = (par ? par->cost + 0.5 * std::ldexp(1.0, -k) : 0.0) + double(s.blocks.size()) * std::ldexp(1.0, -k);
+    };
+    size_t depth_max = 0;
+    for (const std::vector<int> &c : configs) depth_max = std::max(depth_max, c.size());
     // the greedy portfolio (the plain rule, then best-seed growth with affinity windows)
-    // and the staged candidates run as one set of host tasks
+    // runs as host tasks beside the first stages
     const std::pair<int, bool> variants[] = {{0, false}, {0, true}, {1, true}, {2, true}, {3, true}, {6, true}};
     const size_t nport = G ? std::size(variants) : 1;
     std::vector<std::vector<Block>> port(nport);
+    for (size_t depth = 1; depth <= std::max<size_t>(depth_max, 1); ++depth) {
+        const size_t lo = stages.size();
+        for (const std::vector<int> &c : configs) {
+            if (c.size() < depth) continue;
+            std::vector<int> pre(c.begin(), c.begin() + std::ptrdiff_t(depth));
+            if (stage_of.count(pre)) continue;
+            Stage s;
+            s.ks = pre;
+            if (depth > 1) s.parent = stage_of.at(std::vector<int>(pre.begin(), pre.end() - 1));
+            stage_of[pre] = int(stages.size());
+            stages.push_back(std::move(s));
+        }
+        const size_t extra = depth == 1 ? nport : 0;
+        parallel_for(stages.size() - lo + extra, [&](size_t t) {
+            if (t < stages.size() - lo) {
+                block_stage(stages[lo + t]);
+            } else {
+                const size_t task = t - (stages.size() - lo);
+                port[task] = blocking(d, G, k_max, variants[task].first, variants[task].second);
+            }
+        });
+    }
+    // each candidate's rest estimated by a small single-threaded beam (greedy growth alone
+    // cannot tell the candidates apart: on the 34-qubit workload it gives 30 for all, the
+    // beam 26-34)
+    struct Cand {
+        double est = 1e300;
+        int stage = -1;  // its last stage
+    };
     std::vector<Cand> cands(configs.size());
-    // the staged candidates (each about 10 ms of beam search) are handed out first, the short
-    // greedy portfolio runs (a few ms each) fill in behind them
-    parallel_for(nport + cands.size(), [&](size_t t) {
-        if (t >= cands.size()) {
-            const size_t task = t - cands.size();
-            port[task] = blocking(d, G, k_max, variants[task].first, variants[task].second);
-            return;
-        }
-        const size_t task = t + nport;
-        const std::vector<int> &ks = configs[task - nport];
-        Cand c;
-        c.ks = ks;
-        c.head.assign(size_t(n), 0);
-        uint64_t pool = full;
-        double sub_cost = 0.0;
-        for (size_t si = 0; si < ks.size(); ++si) {
-            const uint64_t X = choose_excluded(d, c.head, ks[si], pool, full);
-            std::vector<Block> b = blocking_from(d, G, k_max, 2, true, full & ~X, c.head, c.placed);
-            sub_cost += double(b.size()) * std::ldexp(1.0, -ks[si]);
-            if (si > 0) sub_cost += 0.5 * std::ldexp(1.0, -ks[si]);  // expansion into this sub-state
-            for (Block &x : b) c.pre.push_back(std::move(x));
-            c.stage_end.push_back(int(c.pre.size()));
-            c.X.push_back(X);
-            pool = X;
-        }
-        // the rest estimated by a small single-threaded beam (greedy growth alone cannot tell
-        // the candidates apart: on the 34-qubit workload it gives 30 for all, the beam 28-34)
+    parallel_for(cands.size(), [&](size_t i) {
+        const Stage &s = stages[size_t(stage_of.at(configs[i]))];
         const std::vector<Block> rest =
-            beam_blocking(d, G, k_max, 0, kSmallBeamWidth, kSmallBeamExpand, c.head, c.placed, 1);
-        c.sub_cost = sub_cost;
-        c.est = double(rest.size()) + sub_cost;
-        cands[task - nport] = std::move(c);
+            beam_blocking(d, G, k_max, 0, kSmallBeamWidth, kSmallBeamExpand, s.head, s.placed, 1);
+        cands[i].stage = stage_of.at(configs[i]);
+        cands[i].est = (rest.empty() && s.placed < G ? 1e300 : double(rest.size())) + s.cost;
     });
     std::vector<Block> best = std::move(port[0]);
     for (size_t i = 1; i < port.size(); ++i) {
@@ -584,41 +815,76 @@ Blocking plan_blocks(int n, const std::vector<HostGate> &gates, int k_max, bool 
     Blocking out;
     if (!from_zero) {
         if (G > 0) {
-            std::vector<std::vector<Block>> beams(2);
-            parallel_for(2, [&](size_t i) {
-                beams[i] = beam_blocking(d, G, k_max, i == 0 ? 0 : 2, kBeamWidth, kBeamExpand,
-                                         std::vector<size_t>(size_t(d.n), 0), 0);
+            std::vector<std::vector<Block>> searches(3);
+            std::vector<char> ok(3, 0);
+            parallel_for(3, [&](size_t i) {
+                if (i < 2) {
+                    searches[i] = beam_blocking(d, G, k_max, i == 0 ? 0 : 2, kBeamWidth, kBeamExpand,
+                                                std::vector<size_t>(size_t(d.n), 0), 0);
+                    ok[i] = !searches[i].empty();
+                } else {
+                    ok[i] = closure_beam(d, G, k_max, kClosureWidth, kClosureExpand,
+                                         std::vector<size_t>(size_t(d.n), 0), 0, full, G, &searches[i]);
+                }
             });
-            for (std::vector<Block> &b : beams)
-                if (!b.empty() && b.size() < best.size()) best = std::move(b);
+            for (size_t i = 0; i < searches.size(); ++i)
+                if (ok[i] && searches[i].size() < best.size()) best = std::move(searches[i]);
         }
     } else if (!cands.empty()) {
         const double best_cost = zero_cost(d, best, n, default_span);
-        size_t pi = 0;
-        for (size_t i = 1; i < cands.size(); ++i)
-            if (cands[i].est < cands[pi].est) pi = i;
-        Cand &pick = cands[pi];
-        std::vector<Block> rest_best;
-        {
-            std::vector<size_t> h = pick.head;
-            size_t pl = pick.placed;
-            rest_best = blocking_from(d, G, k_max, 2, true, ~0ull, h, pl);
-        }
-        std::vector<std::vector<Block>> beams(2);
-        parallel_for(2, [&](size_t i) {
-            beams[i] = beam_blocking(d, G, k_max, i == 0 ? 0 : 2, kBeamWidth, kBeamExpand, pick.head, pick.placed);
-        });
-        for (std::vector<Block> &r : beams)
-            if ((!r.empty() || pick.placed == G) && r.size() < rest_best.size()) rest_best = std::move(r);
-        const double cost = pick.sub_cost + double(rest_best.size());
-        if (cost < best_cost) {
-            best = std::move(pick.pre);
-            for (Block &b : rest_best) best.push_back(std::move(b));
-            for (size_t si = 0; si < pick.ks.size(); ++si) {
-                out.spans.push_back(n - pick.ks[si]);
-                out.avoid.push_back(pick.X[si]);
-                out.stage_end.push_back(pick.stage_end[si]);
+        // the finalists: the best estimates (the earlier candidate on ties)
+        std::vector<size_t> rank(cands.size());
+        for (size_t i = 0; i < rank.size(); ++i) rank[i] = i;
+        std::stable_sort(rank.begin(), rank.end(), [&](size_t x, size_t y) { return cands[x].est < cands[y].est; });
+        rank.resize(std::min(rank.size(), size_t(kFinalists)));
+        // each finalist's rest: greedy best-seed growth and the closure search, or, where the
+        // closure search does not apply (too many candidate sets), the two beams over grown blocks
+        constexpr size_t kSearches = 4;
+        std::vector<std::vector<Block>> rests(rank.size() * kSearches);
+        std::vector<char> ok(rests.size(), 0);
+        parallel_for(rank.size() * 2, [&](size_t u) {
+            const Stage &s = stages[size_t(cands[rank[u / 2]].stage)];
+            const size_t t = (u / 2) * kSearches;
+            if (u % 2 == 0) {
+                std::vector<size_t> h = s.head;
+                size_t pl = s.placed;
+                rests[t] = blocking_from(d, G, k_max, 2, true, ~0ull, h, pl);
+                ok[t] = pl == G;
+                return;
             }
+            ok[t + 3] = closure_beam(d, G, k_max, kClosureWidth, kClosureExpand, s.head, s.placed, full, G, &rests[t + 3]);
+            if (ok[t + 3]) return;
+            for (size_t which = 1; which < 3; ++which) {
+                rests[t + which] =
+                    beam_blocking(d, G, k_max, which == 1 ? 0 : 2, kBeamWidth, kBeamExpand, s.head, s.placed);
+                ok[t + which] = !rests[t + which].empty() || s.placed == G;
+            }
+        });
+        size_t pick = rests.size();
+        double pick_cost = 1e300;
+        for (size_t t = 0; t < rests.size(); ++t) {
+            if (!ok[t]) continue;
+            const double cost = stages[size_t(cands[rank[t / kSearches]].stage)].cost + double(rests[t].size());
+            if (cost < pick_cost) {
+                pick_cost = cost;
+                pick = t;
+            }
+        }
+        if (pick < rests.size() && pick_cost < best_cost) {
+            // the stages of the pick, first to last
+            std::vector<int> chain;
+            for (int si = cands[rank[pick / kSearches]].stage; si >= 0; si = stages[size_t(si)].parent)
+                chain.push_back(si);
+            std::reverse(chain.begin(), chain.end());
+            best.clear();
+            for (int si : chain) {
+                Stage &s = stages[size_t(si)];
+                for (Block &b : s.blocks) best.push_back(std::move(b));
+                out.spans.push_back(n - s.ks.back());
+                out.avoid.push_back(s.X);
+                out.stage_end.push_back(int(best.size()));
+            }
+            for (Block &b : rests[pick]) best.push_back(std::move(b));
         }
     }
     out.gates.reserve(best.size());

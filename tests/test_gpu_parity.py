@@ -190,14 +190,14 @@ def test_substate_prefix_is_exact(lib):
     np.testing.assert_array_equal(out[0], out[1])
 
 
+@pytest.mark.parametrize("n,cycles,stages", [(22, 8, 2), (23, 10, 3)])
 @pytest.mark.parametrize("precision", [capi.RCS_PREC_FP32_FUSED, capi.RCS_PREC_BF16X3, capi.RCS_PREC_TF32X3])
-def test_substate_prefix_vs_oracle(lib, oracle, precision):
-    n = 22
-    circ = C.generate(C.grid_for_n(n), cycles=10, pattern="ABCDCDAB", seed=91, jitter=0.05)
+def test_substate_prefix_vs_oracle(lib, oracle, precision, n, cycles, stages):
+    circ = C.generate(C.grid_for_n(n), cycles=cycles, pattern="ABCDCDAB", seed=91, jitter=0.05)
     plan = capi.rcs_plan_build(n, circ.gates, precision)
     info = capi.rcs_plan_info(plan)
-    assert info["prefix_passes"] >= 2 and info["prefix_qubits"] <= n - 2
-    assert info["prefix_stages"] == 2  # nested sub-states, each expanded into the next
+    assert info["prefix_passes"] >= 2 and info["prefix_qubits"] <= n - 1
+    assert info["prefix_stages"] == stages  # nested sub-states, each expanded into the next
     # a tensor-core pass after the sub-states reads the last sub-state itself (expansion and
     # pass in one launch) unless it needs the memory-order kernel (4+ targets below bit 5)
     t_next, _ = capi.rcs_plan_pass(plan, info["prefix_passes"])
