@@ -164,29 +164,33 @@ def test_autotuned_fused_path(lib, oracle):
 def test_substate_prefix_is_exact(lib):
     """From a fresh |0...0> the leading passes run on a compact sub-state and one
     expansion pass writes the whole state. Every slice computes exactly what it
-    computes in the full state, so the result equals the same circuit applied to an
+    computes in the full state, so the result equals the same plan run on an
     explicitly written |0...0> (which is not fresh: no prefix) bit for bit. At 11
-    qubits no layout is chosen, so both runs use the same passes."""
+    qubits the plan carries no layout, so it runs on either state."""
     n = 11
     circ = C.generate(C.grid_for_n(n), cycles=8, pattern="EFGH", seed=93, jitter=0.05)
     plan = capi.rcs_plan_build(n, circ.gates, capi.RCS_PREC_FP32_FUSED, 4)
     info = capi.rcs_plan_info(plan)
-    capi.rcs_plan_destroy(plan)
     assert info["prefix_passes"] >= 2
+    assert (capi.rcs_plan_layout(plan, n) == np.arange(n)).all()
     zero = np.zeros(1 << n, dtype=np.complex64)
     zero[0] = 1
     out = []
-    for fresh in (True, False):
-        ctx = capi.rcs_create(n, capi.RCS_PREC_FP32_FUSED, k_max=4)
-        try:
-            if not fresh:
-                capi.rcs_state_write(ctx, zero)
-            capi.rcs_apply_circuit(ctx, circ.gates)
-            ms, full = capi.rcs_last_pass_timing(ctx)
-            assert full == info["n_passes"] - (info["prefix_passes"] if fresh else 0)
-            out.append(capi.rcs_state_read(ctx))
-        finally:
-            capi.rcs_destroy(ctx)
+    try:
+        for fresh in (True, False):
+            ctx = capi.rcs_create(n, capi.RCS_PREC_FP32_FUSED, k_max=4)
+            try:
+                if not fresh:
+                    capi.rcs_state_write(ctx, zero)
+                capi.rcs_plan_upload(ctx, plan)
+                capi.rcs_plan_run(ctx, plan)
+                ms, full = capi.rcs_last_pass_timing(ctx)
+                assert full == info["n_passes"] - (info["prefix_passes"] if fresh else 0)
+                out.append(capi.rcs_state_read(ctx))
+            finally:
+                capi.rcs_destroy(ctx)
+    finally:
+        capi.rcs_plan_destroy(plan)
     np.testing.assert_array_equal(out[0], out[1])
 
 
