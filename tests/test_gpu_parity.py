@@ -194,7 +194,10 @@ def test_substate_prefix_is_exact(lib):
     np.testing.assert_array_equal(out[0], out[1])
 
 
-@pytest.mark.parametrize("n,cycles,stages", [(22, 8, 2), (23, 10, 3)])
+_PREFIX_WANT = {}  # oracle states of the nested-stage circuits, shared by the precisions
+
+
+@pytest.mark.parametrize("n,cycles,stages", [(22, 8, 2), (25, 10, 3)])
 @pytest.mark.parametrize("precision", [capi.RCS_PREC_FP32_FUSED, capi.RCS_PREC_BF16X3, capi.RCS_PREC_TF32X3])
 def test_substate_prefix_vs_oracle(lib, oracle, precision, n, cycles, stages):
     circ = C.generate(C.grid_for_n(n), cycles=cycles, pattern="ABCDCDAB", seed=91, jitter=0.05)
@@ -217,7 +220,9 @@ def test_substate_prefix_vs_oracle(lib, oracle, precision, n, cycles, stages):
     finally:
         capi.rcs_destroy(ctx)
         capi.rcs_plan_destroy(plan)
-    want = oracle.simulate(n, circ.gates)
+    if (n, cycles) not in _PREFIX_WANT:
+        _PREFIX_WANT[(n, cycles)] = oracle.simulate(n, circ.gates)
+    want = _PREFIX_WANT[(n, cycles)]
     assert infidelity(got, want) <= INFID_TOL
     assert np.abs(got - want).max() <= AMP_TOL
 
