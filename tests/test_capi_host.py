@@ -218,3 +218,76 @@ def test_zero_state_byte_count():
     saved = info["zero_hbm_bytes"] - info2["zero_hbm_bytes"]
     assert n_full // 2 <= info2["pair_passes"] <= info["n_passes"] // 2
     assert 16.0 * 2**n * (n_full // 2) <= saved <= 16.0 * 2**n * info2["pair_passes"]
+
+
+@pytest.mark.parametrize("name,full_max,stages", [("34q_5x7m1_20cyc", 26, 3), ("30q_5x6_14cyc", 17, 3),
+                                                  ("32q_4x8_20cyc", 28, 2)])
+def test_closure_search_pass_counts(name, full_max, stages):
+    """The closure search and the three-stage candidates: at k = 6 the plans from |0...0> keep
+    at most this many full-state passes (the grown-block beams and two-stage candidates alone
+    gave 27, 18 and 29), and their cost in full-pass units is below the previous plans'."""
+    circ = C.config_circuit(name)
+    n = circ.n_qubits
+    plan = capi.rcs_plan_build(n, circ.gates, capi.RCS_PREC_BF16X3)
+    try:
+        info = capi.rcs_plan_info(plan)
+    finally:
+        capi.rcs_plan_destroy(plan)
+    assert info["n_passes"] - info["prefix_passes"] <= full_max
+    assert info["prefix_stages"] == stages
+    previous = {"34q_5x7m1_20cyc": 7.585e12, "30q_5x6_14cyc": 0.325e12, "32q_4x8_20cyc": 1.976e12}[name]
+    assert info["zero_hbm_bytes"] < previous
+
+
+def test_plans_are_deterministic():
+    """The searches run on host threads; every step is merged in index order, so two builds of
+    the same circuit give the same passes, bit for bit."""
+    circ = C.config_circuit("30q_5x6_14cyc")
+    out = []
+    for _ in range(2):
+        plan = capi.rcs_plan_build(30, circ.gates, capi.RCS_PREC_BF16X3)
+        try:
+            info, passes = _plan_passes(plan)
+            out.append((info, passes, capi.rcs_plan_layout(plan, 30)))
+        finally:
+            capi.rcs_plan_destroy(plan)
+    assert out[0][0] == out[1][0]
+    np.testing.assert_array_equal(out[0][2], out[1][2])
+    for (t0, u0), (t1, u1) in zip(out[0][1], out[1][1]):
+        np.testing.assert_array_equal(t0, t1)
+        np.testing.assert_array_equal(u0, u1)
+
+
+@pytest.mark.parametrize("n,layers", [(12, 6), (20, 10)])
+def test_densely_coupled_plan_reproduces_circuit(oracle, lib, n, layers):
+    """fSim gates on random qubit pairs, a fresh pairing per layer: at 12 qubits (32 coupled pairs)
+    the closure search runs over the 829 connected 6-sets of the coupling graph; at 20 qubits (77
+    pairs) there are 25 092, more than the 20 000 it takes, so the planner keeps the grown-block
+    searches alone. Either way the planned passes, applied with the oracle, equal the circuit."""
+    rng = np.random.default_rng(n)
+    gates = []
+    for layer in range(layers):
+        for q in range(n):
+            gates.append(C.make_gate(int(rng.integers(0, 3)), q))
+        perm = rng.permutation(n)
+        for i in range(0, n - 1, 2):
+            gates.append(C.make_gate(C.FSIM, int(perm[i]), int(perm[i + 1]), theta=float(rng.uniform(0, np.pi)),
+                                     phi=float(rng.uniform(0, np.pi))))
+    gates = np.array(gates)
+    want = oracle.simulate(n, gates)
+    for prec in (capi.RCS_PREC_BF16X3, capi.RCS_PREC_FP32_FUSED):
+        plan = capi.rcs_plan_build(n, gates, prec)
+        try:
+            info, passes = _plan_passes(plan)
+            phys = capi.rcs_plan_layout(plan, n)
+        finally:
+            capi.rcs_plan_destroy(plan)
+        psi = oracle.zero_state(n)
+        for targets, U in passes:
+            oracle.apply_matrix(psi, targets, U)
+        idx = np.arange(1 << n)
+        stored = np.zeros(1 << n, dtype=np.int64)
+        for q in range(n):
+            stored |= ((idx >> q) & 1) << int(phys[q])
+        np.testing.assert_allclose(psi[stored], want, atol=1e-12)
+        assert info["n_passes"] < len(gates)
