@@ -291,3 +291,37 @@ def test_densely_coupled_plan_reproduces_circuit(oracle, lib, n, layers):
             stored |= ((idx >> q) & 1) << int(phys[q])
         np.testing.assert_allclose(psi[stored], want, atol=1e-12)
         assert info["n_passes"] < len(gates)
+
+
+@pytest.mark.parametrize("kmax,n,extra", [(2, 16, 0), (3, 16, 0), (5, 17, 0), (7, 16, 0), (6, 17, 2)])
+def test_staged_closure_plans_reproduce_circuit(oracle, lib, kmax, n, extra):
+    """Plans from |0...0> at 16-19 qubits have staged candidates, so the closure search blocks
+    their stages and their rest, at every fusion width. `extra` qubits carry single-qubit gates
+    only (no coupler), which only the search's grown-block moves can place. The planned passes,
+    applied with the oracle, equal the circuit."""
+    circ = C.generate(C.grid_for_n(n), cycles=8, pattern="ABCDCDAB", seed=23, jitter=0.05)
+    gates = list(circ.gates)
+    rng = np.random.default_rng(kmax)
+    for q in range(n, n + extra):
+        for _ in range(5):
+            gates.insert(int(rng.integers(0, len(gates) + 1)), C.make_gate(int(rng.integers(0, 3)), q))
+    gates = np.array(gates)
+    m = n + extra
+    prec = capi.RCS_PREC_BF16X3 if kmax == 6 else capi.RCS_PREC_FP32_FUSED
+    plan = capi.rcs_plan_build(m, gates, prec, 0 if kmax == 6 else kmax)
+    try:
+        info, passes = _plan_passes(plan)
+        phys = capi.rcs_plan_layout(plan, m)
+    finally:
+        capi.rcs_plan_destroy(plan)
+    assert info["prefix_passes"] > 0
+    want = oracle.simulate(m, gates)
+    psi = oracle.zero_state(m)
+    for targets, U in passes:
+        assert len(targets) <= max(kmax, 6 if prec == capi.RCS_PREC_BF16X3 else kmax)
+        oracle.apply_matrix(psi, targets, U)
+    idx = np.arange(1 << m)
+    stored = np.zeros(1 << m, dtype=np.int64)
+    for q in range(m):
+        stored |= ((idx >> q) & 1) << int(phys[q])
+    np.testing.assert_allclose(psi[stored], want, atol=1e-12)
